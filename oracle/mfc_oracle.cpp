@@ -1,0 +1,885 @@
+/*
+ * Plain, slow, single-threaded FP64 CPU oracle for the five-equation
+ * WENO5 / HLLC / TVD-RK3 finite-volume method of arXiv 2503.07953 (MFC 5.0).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The
+ * product path (the CUDA library and its Python binding) never imports,
+ * links or calls it, and this file shares no code, header, table or helper
+ * with that path.
+ *
+ * Every numerical routine is templated on its scalar type:
+ *   double  - the oracle proper;
+ *   Dual    - forward-mode directional derivatives (JVPs) of the same code;
+ *   Cnt     - a double that counts the floating-point operations it performs.
+ *
+ * What it computes (all citations are to the paper):
+ *   * five-equation (Allaire, K = 0) model, Sec. 2.1.1: partial densities
+ *     alpha_i rho_i, mixture momentum rho u, total energy rho E and N_f - 1
+ *     volume fractions alpha_j, with alpha_N = 1 - sum_j alpha_j (mixture
+ *     rules, Sec. 2.1.1);
+ *   * stiffened-gas EOS, Sec. 2.2: rho_i e_i = (p + gamma_i pi_i)/(gamma_i - 1),
+ *     so rho e = Gamma p + Pi with Gamma = sum alpha_i/(gamma_i - 1) and
+ *     Pi = sum alpha_i gamma_i pi_i/(gamma_i - 1);
+ *   * finite-volume semi-discretisation, Sec. 3.1, Eq. (rhs), with
+ *     h(q) = (0, ..., 0, -alpha) so that the alpha rows get + alpha div(u);
+ *   * WENO5 reconstruction of the primitive variables with JS, mapped
+ *     (Henrick) and Z weights, Sec. 3.2.1 and Sec. 4.2.2;
+ *   * HLLC approximate Riemann solver, Sec. 3.2.2 (Toro's star states);
+ *   * ghost cells by periodic wrap, zeroth-order extrapolation or mirror
+ *     with negated normal momentum, Sec. 3.3;
+ *   * third-order TVD Runge-Kutta, Sec. 3.4 (the same tableau as the
+ *     q^{n+1} = q^n + h/6 (k1 + k2 + 4 k3) form of Sec. 4.2.3);
+ *   * CFL time step dt = CFL * min over cells and directions of
+ *     dx_d / (|u_d| + c) with the mixture sound speed.
+ * Readings where the paper is silent are listed in the repository design
+ * notes; each is restated at the routine that uses it.
+ *
+ * State layout used by this oracle (its own, independent of the GPU path):
+ * interior cells only, C order [field][z][y][x], no ghost cells.  Field order:
+ * alpha_1 rho_1 .. alpha_N rho_N, rho u_1 .. rho u_ndim, rho E,
+ * alpha_1 .. alpha_{N-1}.  Primitive order: the same slots holding
+ * alpha_i rho_i, u_d, p, alpha_j.
+ */
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+constexpr int MAXF = 4;
+constexpr int MAXQ = 2 * MAXF + 3;
+
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2 };
+
+}  // namespace
+
+extern "C" {
+/* Problem description, mirrored field by field by the ctypes wrapper. */
+typedef struct {
+    int32_t ndim, nf;
+    int32_t n[3];
+    double lo[3], hi[3];
+    int32_t bc_lo[3], bc_hi[3];
+    double gamma[MAXF], pi_inf[MAXF];
+    int32_t weno;
+    double eps;
+} oc_problem;
+}
+
+namespace {
+
+/* ------------------------------------------------------------------ */
+/* Scalar types                                                        */
+/* ------------------------------------------------------------------ */
+
+struct Dual {
+    double v, d;
+    Dual() : v(0), d(0) {}
+    Dual(double x) : v(x), d(0) {}
+    Dual(double x, double dx) : v(x), d(dx) {}
+    friend Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+    friend Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+    friend Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+    friend Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+    friend Dual operator/(Dual a, Dual b) {
+        double r = a.v / b.v;
+        return Dual(r, (a.d - r * b.d) / b.v);
+    }
+    friend bool operator<(Dual a, Dual b) { return a.v < b.v; }
+    friend bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+    friend bool operator>(Dual a, Dual b) { return a.v > b.v; }
+    friend bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+    friend Dual sqrt(Dual a) {
+        double s = std::sqrt(a.v);
+        return Dual(s, a.d / (2.0 * s));
+    }
+    /* d|x|/dx is taken as +1 at x = 0. */
+    friend Dual fabs(Dual a) { return a.v >= 0 ? a : -a; }
+    Dual& operator+=(Dual b) { return *this = *this + b; }
+};
+
+struct OpCounts {
+    int64_t add, mul, div, sqrt, cmp;
+};
+OpCounts g_ops = {0, 0, 0, 0, 0};
+
+struct Cnt {
+    double v;
+    Cnt() : v(0) {}
+    Cnt(double x) : v(x) {}
+    friend Cnt operator+(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v + b.v); }
+    friend Cnt operator-(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v - b.v); }
+    friend Cnt operator-(Cnt a) { return Cnt(-a.v); }
+    friend Cnt operator*(Cnt a, Cnt b) { g_ops.mul++; return Cnt(a.v * b.v); }
+    friend Cnt operator/(Cnt a, Cnt b) { g_ops.div++; return Cnt(a.v / b.v); }
+    friend bool operator<(Cnt a, Cnt b) { g_ops.cmp++; return a.v < b.v; }
+    friend bool operator<=(Cnt a, Cnt b) { g_ops.cmp++; return a.v <= b.v; }
+    friend bool operator>(Cnt a, Cnt b) { g_ops.cmp++; return a.v > b.v; }
+    friend bool operator>=(Cnt a, Cnt b) { g_ops.cmp++; return a.v >= b.v; }
+    friend Cnt sqrt(Cnt a) { g_ops.sqrt++; return Cnt(std::sqrt(a.v)); }
+    friend Cnt fabs(Cnt a) { g_ops.cmp++; return Cnt(std::fabs(a.v)); }
+    Cnt& operator+=(Cnt b) { return *this = *this + b; }
+};
+
+inline double val(double x) { return x; }
+inline double val(Dual x) { return x.v; }
+inline double val(Cnt x) { return x.v; }
+
+using std::fabs;
+using std::sqrt;
+
+/* min / max that keep the FIRST argument on a tie; the branch taken decides
+ * which derivative a Dual carries. */
+template <class T> inline T tmin(T a, T b) { return (b < a) ? b : a; }
+template <class T> inline T tmax(T a, T b) { return (b > a) ? b : a; }
+template <class T> inline T sq(T a) { return a * a; }
+
+/* ------------------------------------------------------------------ */
+/* Field layout and EOS coefficients                                   */
+/* ------------------------------------------------------------------ */
+
+struct Lay {
+    int nf, nd;
+    int nq() const { return 2 * nf + nd; }
+    int rho(int i) const { return i; }
+    int mom(int d) const { return nf + d; }
+    int E() const { return nf + nd; }
+    int alpha(int j) const { return nf + nd + 1 + j; }
+};
+
+/* Mixture-rule coefficients of Sec. 2.1.1 with the EOS of Sec. 2.2:
+ * rho e = sum_i alpha_i (p + gamma_i pi_i)/(gamma_i - 1) = Gamma p + Pi,
+ * Gamma = sum_i alpha_i g_i,  g_i = 1/(gamma_i - 1),
+ * Pi    = sum_i alpha_i h_i,  h_i = gamma_i pi_i/(gamma_i - 1). */
+struct Eos {
+    int nf;
+    double g[MAXF], h[MAXF];
+    explicit Eos(const oc_problem& P) : nf(P.nf) {
+        for (int i = 0; i < nf; ++i) {
+            g[i] = 1.0 / (P.gamma[i] - 1.0);
+            h[i] = P.gamma[i] * P.pi_inf[i] / (P.gamma[i] - 1.0);
+        }
+    }
+    /* Gamma and Pi from the N_f - 1 stored volume fractions; the last one is
+     * 1 - sum of the others (mixture rule sum alpha_i = 1). */
+    template <class T> void mix(const T* alpha_stored, T& Gamma, T& Pi) const {
+        T s = T(0.0);
+        for (int j = 0; j < nf - 1; ++j) s = s + alpha_stored[j];
+        T aN = T(1.0) - s;
+        Gamma = aN * g[nf - 1];
+        Pi = aN * h[nf - 1];
+        for (int j = 0; j < nf - 1; ++j) {
+            Gamma = Gamma + alpha_stored[j] * g[j];
+            Pi = Pi + alpha_stored[j] * h[j];
+        }
+    }
+};
+
+int g_bad = 0; /* count of non-physical states met (rho <= 0 or c^2 <= 0 / NaN) */
+
+/* Conservative -> primitive (a2): rho = sum alpha_i rho_i, u = (rho u)/rho,
+ * p = (rho E - 1/2 rho |u|^2 - Pi)/Gamma. */
+template <class T>
+void cons_to_prim(const Lay& L, const Eos& eos, const T* q, T* w) {
+    T rho = q[L.rho(0)];
+    for (int i = 1; i < L.nf; ++i) rho = rho + q[L.rho(i)];
+    if (!(val(rho) > 0.0)) g_bad++;
+    for (int i = 0; i < L.nf; ++i) w[L.rho(i)] = q[L.rho(i)];
+    T u2 = T(0.0);
+    for (int d = 0; d < L.nd; ++d) {
+        w[L.mom(d)] = q[L.mom(d)] / rho;
+        u2 = u2 + w[L.mom(d)] * w[L.mom(d)];
+    }
+    for (int j = 0; j < L.nf - 1; ++j) w[L.alpha(j)] = q[L.alpha(j)];
+    T Gamma, Pi;
+    eos.mix(q + L.alpha(0), Gamma, Pi);
+    T ke = T(0.5) * rho * u2;
+    w[L.E()] = (q[L.E()] - ke - Pi) / Gamma;
+}
+
+/* Primitive -> conservative: rho E = Gamma p + Pi + 1/2 rho |u|^2. */
+template <class T>
+void prim_to_cons(const Lay& L, const Eos& eos, const T* w, T* q) {
+    T rho = w[L.rho(0)];
+    for (int i = 1; i < L.nf; ++i) rho = rho + w[L.rho(i)];
+    for (int i = 0; i < L.nf; ++i) q[L.rho(i)] = w[L.rho(i)];
+    T u2 = T(0.0);
+    for (int d = 0; d < L.nd; ++d) {
+        q[L.mom(d)] = rho * w[L.mom(d)];
+        u2 = u2 + w[L.mom(d)] * w[L.mom(d)];
+    }
+    for (int j = 0; j < L.nf - 1; ++j) q[L.alpha(j)] = w[L.alpha(j)];
+    T Gamma, Pi;
+    eos.mix(w + L.alpha(0), Gamma, Pi);
+    q[L.E()] = Gamma * w[L.E()] + Pi + T(0.5) * rho * u2;
+}
+
+/* Mixture sound speed (reading: the mixture behaves as a stiffened gas with
+ * 1/(gamma_m - 1) = Gamma and gamma_m pi_m/(gamma_m - 1) = Pi, so
+ * c^2 = gamma_m (p + pi_m)/rho = ((Gamma + 1) p + Pi)/(Gamma rho); for one
+ * fluid it is the phasic c_i of Sec. 2.1.1). */
+template <class T> T sound_speed(T rho, T p, T Gamma, T Pi) {
+    T c2 = ((Gamma + T(1.0)) * p + Pi) / (Gamma * rho);
+    if (!(val(c2) > 0.0)) g_bad++;
+    return sqrt(c2);
+}
+
+/* ------------------------------------------------------------------ */
+/* WENO5 (Sec. 3.2.1, Sec. 4.2.2)                                      */
+/* ------------------------------------------------------------------ */
+
+/* Reconstruct the value at one edge of the centre cell of the five-cell
+ * stencil f[0..4] = f_{c-2} .. f_{c+2}.  right_edge = true gives the left
+ * state at face c+1/2, false the right state at face c-1/2.
+ * Candidate stencils r = 0, 1, 2 are {c-2,c-1,c}, {c-1,c,c+1}, {c,c+1,c+2};
+ * their third-order polynomials, the Jiang-Shu smoothness indicators and the
+ * ideal weights (1/10, 6/10, 3/10) (mirrored for the other edge) are the
+ * k = 3 uniform-grid case of the generic Lagrange / Delta-f construction of
+ * Sec. 4.2.2.  Nonlinear weights: JS, alpha_r = d_r/(eps + beta_r)^2;
+ * mapped (Henrick 2005, cited in Sec. 3.2.1), the JS weights pushed through
+ * g_r(w) = w (d_r + d_r^2 - 3 d_r w + w^2)/(d_r^2 + w (1 - 2 d_r)) and
+ * renormalised; Z (Sec. 4.2.2, q = 1), alpha_r = d_r (1 + tau/(beta_r + eps)),
+ * tau = |beta_0 - beta_2|.  dbg (optional) receives p[3], beta[3], omega[3]. */
+template <class T>
+T weno5_edge(const T* f, bool right_edge, int variant, double eps, T* dbg = nullptr) {
+    T p[3], beta[3], d[3];
+    if (right_edge) {
+        p[0] = (T(2.0) * f[0] - T(7.0) * f[1] + T(11.0) * f[2]) / T(6.0);
+        p[1] = (-f[1] + T(5.0) * f[2] + T(2.0) * f[3]) / T(6.0);
+        p[2] = (T(2.0) * f[2] + T(5.0) * f[3] - f[4]) / T(6.0);
+        d[0] = T(0.1); d[1] = T(0.6); d[2] = T(0.3);
+    } else {
+        p[0] = (-f[0] + T(5.0) * f[1] + T(2.0) * f[2]) / T(6.0);
+        p[1] = (T(2.0) * f[1] + T(5.0) * f[2] - f[3]) / T(6.0);
+        p[2] = (T(11.0) * f[2] - T(7.0) * f[3] + T(2.0) * f[4]) / T(6.0);
+        d[0] = T(0.3); d[1] = T(0.6); d[2] = T(0.1);
+    }
+    const T c13 = T(13.0 / 12.0), c14 = T(0.25);
+    beta[0] = c13 * sq(f[0] - T(2.0) * f[1] + f[2]) + c14 * sq(f[0] - T(4.0) * f[1] + T(3.0) * f[2]);
+    beta[1] = c13 * sq(f[1] - T(2.0) * f[2] + f[3]) + c14 * sq(f[1] - f[3]);
+    beta[2] = c13 * sq(f[2] - T(2.0) * f[3] + f[4]) + c14 * sq(T(3.0) * f[2] - T(4.0) * f[3] + f[4]);
+
+    T a[3], w[3];
+    if (variant == WENO_Z) {
+        T tau = fabs(beta[0] - beta[2]);
+        for (int r = 0; r < 3; ++r) a[r] = d[r] * (T(1.0) + tau / (beta[r] + T(eps)));
+    } else {
+        for (int r = 0; r < 3; ++r) a[r] = d[r] / sq(T(eps) + beta[r]);
+    }
+    T s = a[0] + a[1] + a[2];
+    for (int r = 0; r < 3; ++r) w[r] = a[r] / s;
+    if (variant == WENO_M) {
+        T gm[3];
+        for (int r = 0; r < 3; ++r)
+            gm[r] = w[r] * (d[r] + d[r] * d[r] - T(3.0) * d[r] * w[r] + w[r] * w[r]) /
+                    (d[r] * d[r] + w[r] * (T(1.0) - T(2.0) * d[r]));
+        T sm = gm[0] + gm[1] + gm[2];
+        for (int r = 0; r < 3; ++r) w[r] = gm[r] / sm;
+    }
+    if (dbg) {
+        for (int r = 0; r < 3; ++r) { dbg[r] = p[r]; dbg[3 + r] = beta[r]; dbg[6 + r] = w[r]; }
+    }
+    return w[0] * p[0] + w[1] * p[1] + w[2] * p[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* HLLC (Sec. 3.2.2)                                                   */
+/* ------------------------------------------------------------------ */
+
+/* HLLC flux across a face with normal along axis d, from the reconstructed
+ * primitive states WL, WR.  Readings (the paper gives the structure only):
+ *  - wave speeds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R);
+ *  - S* from continuity of normal velocity and pressure across the contact;
+ *  - star states U*_K = chi_K (alpha_i rho_i, rho S* / rho u_t,
+ *    rho [E/rho + (S* - u)(S* + p/(rho (S_K - u)))]), chi_K = (S_K - u)/(S_K - S*),
+ *    and F*_K = F_K + S_K (U*_K - U_K) (Toro);
+ *  - side: S* >= 0 takes the left (F_L if S_L >= 0, else F*_L), S* < 0 the
+ *    right (F_R if S_R <= 0, else F*_R);
+ *  - face velocity u_f = u_K outside the fan, S* inside it (the u^{(x)} of
+ *    Sec. 3.2.1); volume-fraction "flux" alpha_f u_f with alpha_f from the
+ *    side taken.
+ * F receives N_q entries (the alpha slots hold alpha_f u_f); uf the face
+ * velocity. */
+template <class T>
+void hllc(const Lay& L, const Eos& eos, int d, const T* WL, const T* WR, T* F, T& uf) {
+    const T* W[2] = {WL, WR};
+    T rho[2], un[2], p[2], E[2], c[2];
+    for (int K = 0; K < 2; ++K) {
+        const T* w = W[K];
+        T r = w[L.rho(0)];
+        for (int i = 1; i < L.nf; ++i) r = r + w[L.rho(i)];
+        T u2 = T(0.0);
+        for (int e = 0; e < L.nd; ++e) u2 = u2 + w[L.mom(e)] * w[L.mom(e)];
+        T Gamma, Pi;
+        eos.mix(w + L.alpha(0), Gamma, Pi);
+        rho[K] = r;
+        un[K] = w[L.mom(d)];
+        p[K] = w[L.E()];
+        E[K] = Gamma * p[K] + Pi + T(0.5) * r * u2;
+        c[K] = sound_speed(r, p[K], Gamma, Pi);
+    }
+    T SL = tmin(un[0] - c[0], un[1] - c[1]);
+    T SR = tmax(un[0] + c[0], un[1] + c[1]);
+    T Ss = (p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1])) /
+           (rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
+
+    int K;
+    T SK;
+    bool star;
+    if (Ss >= T(0.0)) {
+        K = 0; SK = SL; star = SL < T(0.0);
+    } else {
+        K = 1; SK = SR; star = SR > T(0.0);
+    }
+    const T* w = W[K];
+    /* physical flux of side K */
+    for (int i = 0; i < L.nf; ++i) F[L.rho(i)] = w[L.rho(i)] * un[K];
+    for (int e = 0; e < L.nd; ++e) {
+        F[L.mom(e)] = rho[K] * un[K] * w[L.mom(e)];
+        if (e == d) F[L.mom(e)] = F[L.mom(e)] + p[K];
+    }
+    F[L.E()] = (E[K] + p[K]) * un[K];
+    if (star) {
+        T chi = (SK - un[K]) / (SK - Ss);
+        for (int i = 0; i < L.nf; ++i) {
+            T Us = chi * w[L.rho(i)];
+            F[L.rho(i)] = F[L.rho(i)] + SK * (Us - w[L.rho(i)]);
+        }
+        for (int e = 0; e < L.nd; ++e) {
+            T Us = chi * rho[K] * (e == d ? Ss : w[L.mom(e)]);
+            F[L.mom(e)] = F[L.mom(e)] + SK * (Us - rho[K] * w[L.mom(e)]);
+        }
+        T Es = chi * rho[K] * (E[K] / rho[K] + (Ss - un[K]) * (Ss + p[K] / (rho[K] * (SK - un[K]))));
+        F[L.E()] = F[L.E()] + SK * (Es - E[K]);
+        uf = Ss;
+    } else {
+        uf = un[K];
+    }
+    for (int j = 0; j < L.nf - 1; ++j) F[L.alpha(j)] = w[L.alpha(j)] * uf;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ghost cells (Sec. 3.3)                                              */
+/* ------------------------------------------------------------------ */
+
+/* Map index i along axis ax (possibly outside [0, n)) to the interior cell
+ * whose value the ghost cell carries.  Periodic: wrap.  Transmissive
+ * (zeroth-order extrapolation): the nearest interior cell.  Reflective
+ * (symmetry / slip wall): the mirror image, with the normal momentum
+ * negated (flip toggled). */
+inline int bc_map(const oc_problem& P, int ax, int i, bool& flip) {
+    int n = P.n[ax];
+    if (i < 0) {
+        switch (P.bc_lo[ax]) {
+            case BC_PERIODIC: return i + n;
+            case BC_TRANSMISSIVE: return 0;
+            default: flip = !flip; return -1 - i;
+        }
+    }
+    if (i >= n) {
+        switch (P.bc_hi[ax]) {
+            case BC_PERIODIC: return i - n;
+            case BC_TRANSMISSIVE: return n - 1;
+            default: flip = !flip; return 2 * n - 1 - i;
+        }
+    }
+    return i;
+}
+
+struct Idx {
+    int c[3];
+};
+
+inline int64_t lin(const oc_problem& P, int i, int j, int k) {
+    return ((int64_t)k * P.n[1] + j) * P.n[0] + i;
+}
+
+/* Whole-domain storage: the conservative state of every interior cell. */
+template <class T> struct FullView {
+    const oc_problem* P;
+    const T* q;
+    int64_t ncell;
+    void load(int64_t c, T* out) const {
+        int nq = 2 * P->nf + P->ndim;
+        for (int f = 0; f < nq; ++f) out[f] = q[f * ncell + c];
+    }
+};
+
+/* Sparse storage: the conservative state of a set of interior cells. */
+template <class T> struct MapView {
+    const oc_problem* P;
+    const std::unordered_map<int64_t, std::array<T, MAXQ>>* m;
+    void load(int64_t c, T* out) const {
+        const auto& a = m->at(c);
+        int nq = 2 * P->nf + P->ndim;
+        for (int f = 0; f < nq; ++f) out[f] = a[f];
+    }
+};
+
+/* Conservative state of cell (i,j,k) where at most one index lies outside the
+ * domain (a ghost cell along that axis). */
+template <class T, class View>
+void fetch(const View& V, const Lay& L, int i, int j, int k, T* out) {
+    const oc_problem& P = *V.P;
+    int idx[3] = {i, j, k};
+    bool flip[3] = {false, false, false};
+    for (int ax = 0; ax < 3; ++ax) idx[ax] = bc_map(P, ax, idx[ax], flip[ax]);
+    V.load(lin(P, idx[0], idx[1], idx[2]), out);
+    for (int ax = 0; ax < L.nd; ++ax)
+        if (flip[ax]) out[L.mom(ax)] = -out[L.mom(ax)];
+}
+
+/* Flux and face velocity at the face between cell c and c + e_ax.  The six
+ * cells c-2 .. c+3 along ax are converted to primitives, the left state is
+ * reconstructed from c-2..c+2 and the right state from c-1..c+3, and the
+ * HLLC solver gives the flux. */
+template <class T, class View>
+void face_flux(const View& V, const Lay& L, const Eos& eos, int ax, const int* c, T* F, T& uf) {
+    const oc_problem& P = *V.P;
+    T W[6][MAXQ], q[MAXQ];
+    for (int m = 0; m < 6; ++m) {
+        int cc[3] = {c[0], c[1], c[2]};
+        cc[ax] += m - 2;
+        fetch<T>(V, L, cc[0], cc[1], cc[2], q);
+        cons_to_prim(L, eos, q, W[m]);
+    }
+    T WL[MAXQ], WR[MAXQ], f[5];
+    for (int k = 0; k < L.nq(); ++k) {
+        for (int m = 0; m < 5; ++m) f[m] = W[m][k];
+        WL[k] = weno5_edge(f, true, P.weno, P.eps);
+        for (int m = 0; m < 5; ++m) f[m] = W[m + 1][k];
+        WR[k] = weno5_edge(f, false, P.weno, P.eps);
+    }
+    hllc(L, eos, ax, WL, WR, F, uf);
+}
+
+inline double dx_of(const oc_problem& P, int ax) { return (P.hi[ax] - P.lo[ax]) / P.n[ax]; }
+
+/* Contribution of direction ax to the right-hand side of cell c, Eq. (rhs):
+ * (F_{c-1/2} - F_{c+1/2})/dx, plus alpha_c (u_{c+1/2} - u_{c-1/2})/dx for the
+ * volume-fraction rows (the -h(q) div u term with h = (0,..,0,-alpha)). */
+template <class T>
+void cell_term(const Lay& L, double dx, const T* Fm, T um, const T* Fp, T up, const T* qc, T* t) {
+    for (int k = 0; k < L.nq(); ++k) t[k] = (Fm[k] - Fp[k]) / T(dx);
+    for (int j = 0; j < L.nf - 1; ++j) {
+        int k = L.alpha(j);
+        t[k] = t[k] + qc[k] * (up - um) / T(dx);
+    }
+}
+
+/* Right-hand side L(q) on every interior cell. */
+template <class T>
+void rhs_full(const oc_problem& P, const T* q, T* Lout) {
+    Lay L{P.nf, P.ndim};
+    Eos eos(P);
+    const int nq = L.nq();
+    const int64_t ncell = (int64_t)P.n[0] * P.n[1] * P.n[2];
+    FullView<T> V{&P, q, ncell};
+    for (int64_t i = 0; i < (int64_t)nq * ncell; ++i) Lout[i] = T(0.0);
+    for (int ax = 0; ax < P.ndim; ++ax) {
+        const int n = P.n[ax];
+        const double dx = dx_of(P, ax);
+        std::vector<std::array<T, MAXQ>> F(n + 1);
+        std::vector<T> uf(n + 1);
+        /* iterate over the lines along ax */
+        int t1 = (ax == 0) ? 1 : 0, t2 = (ax == 2) ? 1 : 2;
+        for (int b = 0; b < P.n[t2]; ++b)
+            for (int a = 0; a < P.n[t1]; ++a) {
+                int c[3];
+                c[t1] = a;
+                c[t2] = b;
+                for (int s = -1; s < n; ++s) { /* face s+1/2, stored at s+1 */
+                    c[ax] = s;
+                    face_flux(V, L, eos, ax, c, F[s + 1].data(), uf[s + 1]);
+                }
+                for (int s = 0; s < n; ++s) {
+                    c[ax] = s;
+                    int64_t cl = lin(P, c[0], c[1], c[2]);
+                    T qc[MAXQ], t[MAXQ];
+                    V.load(cl, qc);
+                    cell_term(L, dx, F[s].data(), uf[s], F[s + 1].data(), uf[s + 1], qc, t);
+                    for (int k = 0; k < nq; ++k) Lout[k * ncell + cl] = Lout[k * ncell + cl] + t[k];
+                }
+            }
+    }
+}
+
+/* Right-hand side at a single interior cell (both faces per direction are
+ * computed by face_flux exactly as rhs_full does, so the result is bitwise
+ * identical to rhs_full at that cell). */
+template <class T, class View>
+void rhs_cell(const View& V, const Lay& L, const Eos& eos, const int* c, T* Lc) {
+    const oc_problem& P = *V.P;
+    for (int k = 0; k < L.nq(); ++k) Lc[k] = T(0.0);
+    T qc[MAXQ];
+    fetch<T>(V, L, c[0], c[1], c[2], qc);
+    for (int ax = 0; ax < P.ndim; ++ax) {
+        T Fm[MAXQ], Fp[MAXQ], um, up, t[MAXQ];
+        int cm[3] = {c[0], c[1], c[2]};
+        cm[ax] -= 1;
+        face_flux(V, L, eos, ax, cm, Fm, um);
+        face_flux(V, L, eos, ax, c, Fp, up);
+        cell_term(L, dx_of(P, ax), Fm, um, Fp, up, qc, t);
+        for (int k = 0; k < L.nq(); ++k) Lc[k] = Lc[k] + t[k];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* TVD-RK3 (Sec. 3.4)                                                  */
+/* ------------------------------------------------------------------ */
+
+/* Shu-Osher form:
+ *   q1 = qn + dt L(qn)
+ *   q2 = 3/4 qn + 1/4 (q1 + dt L(q1))
+ *   q^{n+1} = 1/3 qn + 2/3 (q2 + dt L(q2)). */
+const double RK_A2 = 0.75, RK_B2 = 0.25, RK_A3 = 1.0 / 3.0, RK_B3 = 2.0 / 3.0;
+
+template <class T, class RhsFn>
+void rk3_generic(int64_t n, T* q, double dt, RhsFn rhs) {
+    std::vector<T> q1(n), q2(n), Lb(n);
+    rhs(q, Lb.data());
+    for (int64_t i = 0; i < n; ++i) q1[i] = q[i] + T(dt) * Lb[i];
+    rhs(q1.data(), Lb.data());
+    for (int64_t i = 0; i < n; ++i) q2[i] = T(RK_A2) * q[i] + T(RK_B2) * (q1[i] + T(dt) * Lb[i]);
+    rhs(q2.data(), Lb.data());
+    for (int64_t i = 0; i < n; ++i) q[i] = T(RK_A3) * q[i] + T(RK_B3) * (q2[i] + T(dt) * Lb[i]);
+}
+
+template <class T> void rk3_step(const oc_problem& P, T* q, double dt) {
+    const int nq = 2 * P.nf + P.ndim;
+    const int64_t n = (int64_t)nq * P.n[0] * P.n[1] * P.n[2];
+    rk3_generic(n, q, dt, [&](const T* in, T* out) { rhs_full(P, in, out); });
+}
+
+/* CFL time step: CFL * min over interior cells and active directions of
+ * dx_d / (|u_d| + c) (the paper states the CFL form of neither). */
+template <class T> double cfl_dt(const oc_problem& P, const T* q, double cfl) {
+    Lay L{P.nf, P.ndim};
+    Eos eos(P);
+    const int nq = L.nq();
+    const int64_t ncell = (int64_t)P.n[0] * P.n[1] * P.n[2];
+    FullView<T> V{&P, q, ncell};
+    double m = INFINITY;
+    for (int64_t c = 0; c < ncell; ++c) {
+        T qc[MAXQ], w[MAXQ];
+        V.load(c, qc);
+        cons_to_prim(L, eos, qc, w);
+        T rho = qc[L.rho(0)];
+        for (int i = 1; i < L.nf; ++i) rho = rho + qc[L.rho(i)];
+        T Gamma, Pi;
+        eos.mix(qc + L.alpha(0), Gamma, Pi);
+        T cs = sound_speed(rho, w[L.E()], Gamma, Pi);
+        for (int ax = 0; ax < P.ndim; ++ax) {
+            T s = T(dx_of(P, ax)) / (fabs(w[L.mom(ax)]) + cs);
+            m = std::min(m, val(s));
+        }
+        (void)nq;
+    }
+    return cfl * m;
+}
+
+int check_problem(const oc_problem* P) {
+    if (!P) return -1;
+    if (P->ndim < 1 || P->ndim > 3 || P->nf < 1 || P->nf > MAXF) return -1;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax < P->ndim) {
+            if (P->n[ax] < 1) return -1;
+            if (!(P->hi[ax] > P->lo[ax])) return -1;
+            for (int s = 0; s < 2; ++s) {
+                int bc = s ? P->bc_hi[ax] : P->bc_lo[ax];
+                if (bc < 0 || bc > 2) return -1;
+                if (bc != BC_TRANSMISSIVE && P->n[ax] < 3) return -1;
+            }
+            if ((P->bc_lo[ax] == BC_PERIODIC) != (P->bc_hi[ax] == BC_PERIODIC)) return -1;
+        } else if (P->n[ax] != 1) {
+            return -1;
+        }
+    }
+    for (int i = 0; i < P->nf; ++i)
+        if (!(P->gamma[i] > 1.0) || !(P->pi_inf[i] >= 0.0)) return -1;
+    if (P->weno < 0 || P->weno > 2 || !(P->eps > 0.0)) return -1;
+    return 0;
+}
+
+inline int64_t ncells(const oc_problem* P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
+inline int nfields(const oc_problem* P) { return 2 * P->nf + P->ndim; }
+
+}  // namespace
+
+/* ------------------------------------------------------------------ */
+/* C entry points (ctypes)                                             */
+/* ------------------------------------------------------------------ */
+extern "C" {
+
+int oc_nfields(const oc_problem* P) { return check_problem(P) ? -1 : nfields(P); }
+
+int oc_prim_to_cons(const oc_problem* P, const double* w, double* q) {
+    if (check_problem(P)) return -1;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    int64_t nc = ncells(P);
+    for (int64_t c = 0; c < nc; ++c) {
+        double wi[MAXQ], qo[MAXQ];
+        for (int k = 0; k < L.nq(); ++k) wi[k] = w[k * nc + c];
+        prim_to_cons(L, eos, wi, qo);
+        for (int k = 0; k < L.nq(); ++k) q[k * nc + c] = qo[k];
+    }
+    return 0;
+}
+
+int oc_cons_to_prim(const oc_problem* P, const double* q, double* w) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    int64_t nc = ncells(P);
+    for (int64_t c = 0; c < nc; ++c) {
+        double qi[MAXQ], wo[MAXQ];
+        for (int k = 0; k < L.nq(); ++k) qi[k] = q[k * nc + c];
+        cons_to_prim(L, eos, qi, wo);
+        for (int k = 0; k < L.nq(); ++k) w[k * nc + c] = wo[k];
+    }
+    return g_bad;
+}
+
+/* Returns dt (> 0), or -1 on a bad problem. */
+double oc_dt(const oc_problem* P, const double* q, double cfl) {
+    if (check_problem(P)) return -1.0;
+    return cfl_dt(*P, q, cfl);
+}
+
+/* L(q) on every interior cell.  Returns the number of non-physical states met. */
+int oc_rhs(const oc_problem* P, const double* q, double* Lout) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    rhs_full(*P, q, Lout);
+    return g_bad;
+}
+
+/* One RK3 step in place with the given dt. */
+int oc_rk3_step(const oc_problem* P, double* q, double dt) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    rk3_step(*P, q, dt);
+    return g_bad;
+}
+
+/* nsteps RK3 steps in place.  dt_in (nullable): fixed per-step dt; else the
+ * CFL dt of each step's initial state.  dt_out (nullable) receives the dts. */
+int oc_rk3_run(const oc_problem* P, double* q, int nsteps, double cfl, const double* dt_in, double* dt_out) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        double dt = dt_in ? dt_in[s] : cfl_dt(*P, q, cfl);
+        if (dt_out) dt_out[s] = dt;
+        rk3_step(*P, q, dt);
+    }
+    return g_bad;
+}
+
+/* Forward-mode derivative of L: dL = (dL/dq) dq. */
+int oc_rhs_jvp(const oc_problem* P, const double* q, const double* dq, double* Lout, double* dL) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    int64_t n = (int64_t)nfields(P) * ncells(P);
+    std::vector<Dual> qd(n), Ld(n);
+    for (int64_t i = 0; i < n; ++i) qd[i] = Dual(q[i], dq[i]);
+    rhs_full(*P, qd.data(), Ld.data());
+    for (int64_t i = 0; i < n; ++i) {
+        if (Lout) Lout[i] = Ld[i].v;
+        dL[i] = Ld[i].d;
+    }
+    return g_bad;
+}
+
+/* Forward-mode derivative of one RK3 step at fixed dt, in place on (q, dq). */
+int oc_rk3_step_jvp(const oc_problem* P, double* q, double* dq, double dt) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    int64_t n = (int64_t)nfields(P) * ncells(P);
+    std::vector<Dual> qd(n);
+    for (int64_t i = 0; i < n; ++i) qd[i] = Dual(q[i], dq[i]);
+    rk3_step(*P, qd.data(), dt);
+    for (int64_t i = 0; i < n; ++i) {
+        q[i] = qd[i].v;
+        dq[i] = qd[i].d;
+    }
+    return g_bad;
+}
+
+/* One RK3 step evaluated only at the listed cells, through their domain of
+ * dependence: stage 3 at the cell needs q2 on its stencil, stage 2 there
+ * needs q1 on theirs.  cells holds (i, j, k) triples; out receives
+ * ncell_out x nfields values (cell-major).  Same arithmetic as oc_rk3_step. */
+int oc_rk3_step_sampled(const oc_problem* P, const double* q, double dt, int64_t nsample,
+                        const int64_t* cells, double* out) {
+    if (check_problem(P)) return -1;
+    g_bad = 0;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    const int nq = L.nq();
+    const int64_t nc = ncells(P);
+    FullView<double> V0{P, q, nc};
+    auto decode = [&](int64_t c, int* ijk) {
+        ijk[0] = (int)(c % P->n[0]);
+        ijk[1] = (int)((c / P->n[0]) % P->n[1]);
+        ijk[2] = (int)(c / ((int64_t)P->n[0] * P->n[1]));
+    };
+    auto closure = [&](const std::unordered_set<int64_t>& S) {
+        std::unordered_set<int64_t> R = S;
+        for (int64_t c : S) {
+            int ijk[3];
+            decode(c, ijk);
+            for (int ax = 0; ax < P->ndim; ++ax)
+                for (int m = -3; m <= 3; ++m) {
+                    int id[3] = {ijk[0], ijk[1], ijk[2]};
+                    bool fl = false;
+                    id[ax] = bc_map(*P, ax, id[ax] + m, fl);
+                    R.insert(lin(*P, id[0], id[1], id[2]));
+                }
+        }
+        return R;
+    };
+    for (int64_t s = 0; s < nsample; ++s) {
+        int tgt[3] = {(int)cells[3 * s], (int)cells[3 * s + 1], (int)cells[3 * s + 2]};
+        for (int ax = 0; ax < 3; ++ax)
+            if (tgt[ax] < 0 || tgt[ax] >= P->n[ax]) return -1;
+        std::unordered_set<int64_t> S3 = {lin(*P, tgt[0], tgt[1], tgt[2])};
+        auto S2 = closure(S3);
+        auto S1 = closure(S2);
+        std::unordered_map<int64_t, std::array<double, MAXQ>> m1, m2;
+        for (int64_t c : S1) {
+            int ijk[3];
+            decode(c, ijk);
+            double Lc[MAXQ], qc[MAXQ];
+            rhs_cell(V0, L, eos, ijk, Lc);
+            V0.load(c, qc);
+            std::array<double, MAXQ> a{};
+            for (int k = 0; k < nq; ++k) a[k] = qc[k] + dt * Lc[k];
+            m1[c] = a;
+        }
+        MapView<double> V1{P, &m1};
+        for (int64_t c : S2) {
+            int ijk[3];
+            decode(c, ijk);
+            double Lc[MAXQ], qc[MAXQ];
+            rhs_cell(V1, L, eos, ijk, Lc);
+            V0.load(c, qc);
+            std::array<double, MAXQ> a{};
+            for (int k = 0; k < nq; ++k) a[k] = RK_A2 * qc[k] + RK_B2 * (m1[c][k] + dt * Lc[k]);
+            m2[c] = a;
+        }
+        MapView<double> V2{P, &m2};
+        {
+            double Lc[MAXQ], qc[MAXQ];
+            int64_t c = *S3.begin();
+            rhs_cell(V2, L, eos, tgt, Lc);
+            V0.load(c, qc);
+            for (int k = 0; k < nq; ++k) out[s * nq + k] = RK_A3 * qc[k] + RK_B3 * (m2[c][k] + dt * Lc[k]);
+        }
+    }
+    return g_bad;
+}
+
+/* Floating-point operations of one RK3 step (incl. the CFL dt when cfl > 0),
+ * as the oracle performs them: counts = {add/sub, mul, div, sqrt, cmp}. */
+int oc_rk3_step_count(const oc_problem* P, const double* q, double dt, int64_t* counts) {
+    if (check_problem(P)) return -1;
+    int64_t n = (int64_t)nfields(P) * ncells(P);
+    std::vector<Cnt> qc(n);
+    for (int64_t i = 0; i < n; ++i) qc[i] = Cnt(q[i]);
+    g_ops = {0, 0, 0, 0, 0};
+    rk3_step(*P, qc.data(), dt);
+    counts[0] = g_ops.add; counts[1] = g_ops.mul; counts[2] = g_ops.div;
+    counts[3] = g_ops.sqrt; counts[4] = g_ops.cmp;
+    return 0;
+}
+
+/* Operation counts of each building block, one call each, on the given cell
+ * states (conservative qa, qb of two neighbouring cells; the face uses qa as
+ * the left and qb as the right primitive state after conversion):
+ * row 0 cons_to_prim, row 1 one WENO5 edge value, row 2 HLLC, row 3 the cell
+ * term of one direction, row 4 one RK3 stage update of one cell (the costlier
+ * stage form a*qn + b*(q + dt*L)), row 5 the CFL quantity of one cell.
+ * out: 6 rows x 5 counts. */
+int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int64_t* out) {
+    if (check_problem(P)) return -1;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    const int nq = L.nq();
+    Cnt a[MAXQ], b[MAXQ], wa[MAXQ], wb[MAXQ], F[MAXQ], uf;
+    for (int k = 0; k < nq; ++k) { a[k] = Cnt(qa[k]); b[k] = Cnt(qb[k]); }
+    auto take = [&](int row) {
+        out[row * 5 + 0] = g_ops.add; out[row * 5 + 1] = g_ops.mul; out[row * 5 + 2] = g_ops.div;
+        out[row * 5 + 3] = g_ops.sqrt; out[row * 5 + 4] = g_ops.cmp;
+        g_ops = {0, 0, 0, 0, 0};
+    };
+    g_ops = {0, 0, 0, 0, 0};
+    cons_to_prim(L, eos, a, wa);
+    take(0);
+    cons_to_prim(L, eos, b, wb);
+    g_ops = {0, 0, 0, 0, 0};
+    Cnt f[5] = {wa[0], wb[0], wa[0], wb[0], wa[0]};
+    weno5_edge(f, true, P->weno, P->eps);
+    take(1);
+    hllc(L, eos, 0, wa, wb, F, uf);
+    take(2);
+    Cnt t[MAXQ];
+    cell_term(L, 1.0, F, uf, F, uf, a, t);
+    take(3);
+    for (int k = 0; k < nq; ++k) t[k] = Cnt(RK_A2) * a[k] + Cnt(RK_B2) * (b[k] + Cnt(1e-3) * F[k]);
+    take(4);
+    {
+        Cnt rho = a[L.rho(0)];
+        for (int i = 1; i < L.nf; ++i) rho = rho + a[L.rho(i)];
+        Cnt Gamma, Pi;
+        eos.mix(a + L.alpha(0), Gamma, Pi);
+        Cnt cs = sound_speed(rho, wa[L.E()], Gamma, Pi);
+        for (int ax = 0; ax < P->ndim; ++ax) {
+            Cnt s = Cnt(1.0) / (fabs(wa[L.mom(ax)]) + cs);
+            (void)s;
+        }
+    }
+    take(5);
+    return 0;
+}
+
+/* One WENO5 stencil, for pinning the constants and weights:
+ * out[0..2] candidate values at the right edge, [3..5] beta, [6..8] weights,
+ * [9] right-edge value; [10..12] candidates at the left edge, [13..15]
+ * weights, [16] left-edge value. */
+void oc_weno5_detail(int variant, double eps, const double* f, double* out) {
+    double dbg[9];
+    out[9] = weno5_edge(f, true, variant, eps, dbg);
+    for (int i = 0; i < 9; ++i) out[i] = dbg[i];
+    out[16] = weno5_edge(f, false, variant, eps, dbg);
+    for (int i = 0; i < 3; ++i) { out[10 + i] = dbg[i]; out[13 + i] = dbg[6 + i]; }
+}
+
+/* HLLC flux for one face from primitive states (N_q each) along axis dir. */
+int oc_hllc_face(const oc_problem* P, int dir, const double* WL, const double* WR, double* F, double* uf) {
+    if (check_problem(P) || dir < 0 || dir >= P->ndim) return -1;
+    g_bad = 0;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    double u;
+    hllc(L, eos, dir, WL, WR, F, u);
+    *uf = u;
+    return g_bad;
+}
+
+/* The RK3 combination applied to the scalar linear ODE y' = lambda y. */
+double oc_rk3_linear(double lambda, double y0, double dt) {
+    double y = y0;
+    rk3_generic(1, &y, dt, [&](const double* in, double* out) { out[0] = lambda * in[0]; });
+    return y;
+}
+
+}  /* extern "C" */
