@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the five-equation WENO5 / HLLC / TVD-RK3 step on GB300.
+
+Default workload: the 3D two-fluid shock-bubble interaction on 256^3 cells
+(7 conserved fields, Mach 1.5 shock, light-gas sphere, seeded density
+noise), FP64, CFL 0.4 with the CFL dt computed on the device every step.
+One timed "step" is one full RK3 step (CFL reduction + three stages of
+three directional sweeps).  The state is 1.0 GB, far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+replica of the workload (the method needs no data exchange on one GPU);
+value = all ranks' cell updates / the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_07953_gb300 import flops  # noqa: E402
+from paper_2503_07953_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "WENO5-HLLC cell-updates/s per RK3 step, FP64 vs mixed at stated error; VJP/fwd cost"
+UNIT = "cell-updates/s"
+# FP64 peak from unit counts and clock: 152 SMs x 2 DFMA lanes x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shock_bubble_3d",
+                    choices=["shock_bubble_3d", "random_interfaces_3d", "bubble_collapse_2d", "water_air_1d"])
+    ap.add_argument("--n", type=int, default=0, help="cells per axis (0: the workload's own size)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed, adjoint, e2e and CPU legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return args
+
+
+def make_workload(name: str, n: int):
+    if name == "shock_bubble_3d":
+        return wl.shock_bubble_3d(n or 256)
+    if name == "random_interfaces_3d":
+        return wl.random_interfaces_3d(n or 512)
+    if name == "bubble_collapse_2d":
+        return wl.bubble_collapse_2d(n or 1024)
+    return wl.water_air_shock_tube(n or 1000)
+
+
+def describe(case) -> str:
+    dims = "x".join(str(x) for x in case.n)
+    return f"{case.name} {dims} cells, {case.nq} fields, {case.nf} fluids, WENO5-M + HLLC, TVD-RK3, CFL {case.cfl}"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def launches_per_step(nd: int) -> int:
+    # set-scalars + CFL reduction + finalize + 3 stages x nd sweeps
+    return 3 + 3 * nd
+
+
+def time_steps(S, q, steps: int) -> float:
+    """Milliseconds for `steps` RK3 steps, CUDA events on the launching stream."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        S.rk3_step(q, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_sweeps(S, q, reps: int) -> float:
+    """Average milliseconds of one directional sweep launch: `reps`
+    evaluations of L (ndim sweep launches each, nothing else)."""
+    out = S.empty()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        S.rhs(q, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        S.rhs(q, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (reps * S.ndim)
+
+
+def field_errors(a: torch.Tensor, b: torch.Tensor):
+    out = []
+    for k in range(b.shape[0]):
+        den = b[k].abs().max().item()
+        out.append((a[k] - b[k]).abs().max().item() / den if den > 0 else 0.0)
+    return out
+
+
+def cpu_baseline_leg(workload: str, sample_n: int, steps: int) -> dict:
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+    oracle.build()
+    if workload == "shock_bubble_3d":
+        case, W = wl.shock_bubble_3d(dims=(sample_n,) * 3)
+    elif workload == "random_interfaces_3d":
+        case, W = wl.random_interfaces_3d(dims=(sample_n,) * 3)
+    elif workload == "bubble_collapse_2d":
+        case, W = wl.bubble_collapse_2d(dims=(sample_n * 8, sample_n * 8))
+    else:
+        case, W = wl.water_air_shock_tube(1000)
+    P = oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
+                       bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
+    q = oracle.prim_to_cons(P, W)
+    t0 = time.perf_counter()
+    q, dts = oracle.rk3_run(P, q, steps, cfl=case.cfl)
+    el = time.perf_counter() - t0
+    cells = case.ncells
+    return {"value": cells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{case.name} {'x'.join(map(str, case.n))} cells, {steps} RK3 steps "
+                      f"(CFL dt each step), single-threaded, {el:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the plain CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sample_n = 40
+    if args.workload == "shock_bubble_3d":
+        case, W = wl.shock_bubble_3d(dims=(sample_n,) * 3)
+    elif args.workload == "random_interfaces_3d":
+        case, W = wl.random_interfaces_3d(dims=(sample_n,) * 3)
+    elif args.workload == "bubble_collapse_2d":
+        case, W = wl.bubble_collapse_2d(dims=(256, 256))
+    else:
+        case, W = wl.water_air_shock_tube(1000)
+    P = oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
+                       bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
+    q = oracle.prim_to_cons(P, W)
+    q, _ = oracle.rk3_run(P, q, args.warmup, cfl=case.cfl)
+    t0 = time.perf_counter()
+    q, _ = oracle.rk3_run(P, q, args.steps, cfl=case.cfl)
+    el = time.perf_counter() - t0
+    value = case.ncells * args.steps / el
+    sample = f"{case.name} {'x'.join(map(str, case.n))} cells per step (bounded sample of the workload), single-threaded"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": describe(make_workload_stub(args)), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_workload_stub(args):
+    """The workload description without generating its fields."""
+    n = args.n
+    table = {"shock_bubble_3d": ([n or 256] * 3, 7, 2, 0.4), "random_interfaces_3d": ([n or 512] * 3, 9, 3, 0.4),
+             "bubble_collapse_2d": ([n or 1024] * 2, 6, 2, 0.3), "water_air_1d": ([n or 1000], 5, 2, 0.3)}
+    dims, nq, nf, cfl = table[args.workload]
+
+    class _C:
+        pass
+    c = _C()
+    c.name, c.n, c.nq, c.nf, c.cfl = args.workload, dims, nq, nf, cfl
+    return c
+
+
+def run_ours(args, world, rank, local):
+    from paper_2503_07953_gb300 import build, mfc
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    case, W = make_workload(args.workload, args.n)
+    prec = mfc.MFC_MIXED if args.precision == "mixed" else mfc.MFC_FP64
+    S = mfc.Solver.from_case(case, precision=prec)
+    q0 = S.prim_to_cons(S.from_interior(W))
+    del W
+    q = q0.clone()
+    ncell = case.ncells
+
+    # warm-up, then the timed region (CFL dt on the device every step)
+    for _ in range(args.warmup):
+        S.rk3_step(q, 0.0)
+    S.check()
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    ms = time_steps(S, q, args.steps)
+    clk = clocks.stop()
+    barrier(world)
+    S.check()
+    ms = max_over_ranks(world, ms)
+    value = world * ncell * args.steps / (ms / 1e3)
+
+    # dominant kernel: the directional sweep (per launch, CUDA events)
+    t_sweep = time_sweeps(S, q, 5)
+    per_sweep = flops.per_cell_sweep(args.workload) * ncell
+    achieved = per_sweep / (t_sweep / 1e3) / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == mfc.MFC_FP64 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if peak else None, "traffic": None,
+            "kernel": f"sweep_kernel ({'FP64' if prec == mfc.MFC_FP64 else 'mixed'}), "
+                      f"{t_sweep:.3f} ms per launch, {per_sweep / 1e9:.2f} GFLOP per launch",
+            "peak_basis": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)"}
+    if prec == mfc.MFC_MIXED:
+        roof["peak_basis"] = "mixed path: FP32 and FP64 pipes both in use, see DESIGN.md"
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == mfc.MFC_FP64 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": describe(case), "cells": ncell, "precision": args.precision,
+                       "dt": "CFL dt reduced on the device every step",
+                       "l2": "state 1.0 GB per buffer > 129 MB L2: no flush needed" if ncell >= 2 ** 22
+                       else "state smaller than L2", "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches_per_step(case.ndim) * args.steps, "clocks": clk, "roofline": roof,
+            "grind_time_ns": (ms / args.steps) * 1e6 / (ncell * case.nq * 3)}
+
+    if not args.no_extras and rank == 0:
+        extras = {}
+        # mixed precision on the same workload, and its error against FP64
+        if prec == mfc.MFC_FP64:
+            Sm = mfc.Solver.from_case(case, precision=mfc.MFC_MIXED)
+            qm = q0.clone()
+            for _ in range(args.warmup):
+                Sm.rk3_step(qm, 0.0)
+            msm = time_steps(Sm, qm, args.steps)
+            Sm.check()
+            # error after warmup + steps steps from the same initial state
+            qf = q0.clone()
+            S.rk3_run(qf, args.warmup + args.steps, 0.0)
+            errs = field_errors(Sm.interior(qm), S.interior(qf))
+            t_sw_m = time_sweeps(Sm, qm, 5)
+            extras["mixed"] = {"value": ncell * args.steps / (msm / 1e3), "ms_per_step": msm / args.steps,
+                               "speedup_vs_fp64": ms / msm,
+                               "field_max_rel_err_vs_fp64": errs,
+                               "after_steps": args.warmup + args.steps,
+                               "sweep_ms_per_launch": t_sw_m}
+            del Sm, qm, qf
+        # end to end through the public API with host buffers
+        host_in = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
+        host_in.copy_(q0)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qd = S.empty()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            qd.copy_(host_in, non_blocking=True)
+            S.rk3_step(qd, 0.0)
+            host_out.copy_(qd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = e0.elapsed_time(e1)
+        nbytes = q.numel() * 8
+        line["e2e"] = {"value": ncell * args.steps / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes}
+        del host_in, host_out, qd
+        torch.cuda.empty_cache()
+        line.update(extras)
+        sample_n = 64 if case.ndim == 3 else 0
+        line["cpu_baseline"] = cpu_baseline_leg(args.workload, sample_n, 5 if case.ndim == 3 else 50)
+    print(json.dumps(line), flush=True) if rank == 0 else None
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

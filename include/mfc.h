@@ -1,0 +1,170 @@
+/*
+ * mfc.h - C ABI of the GB300 (sm_103a) library for the finite-volume
+ * right-hand side of the five-equation diffuse-interface model of
+ * arXiv 2503.07953 (MFC 5.0), time-stepped with third-order TVD Runge-Kutta.
+ *
+ * What the library computes (citations are to the paper):
+ *   state q per cell (Sec. 2.1.1): alpha_1 rho_1 .. alpha_N rho_N,
+ *     rho u_1 .. rho u_ndim, rho E, alpha_1 .. alpha_{N-1}
+ *     (alpha_N = 1 - sum of the others, mixture rules of Sec. 2.1.1);
+ *   EOS: stiffened gas per fluid (Sec. 2.2);
+ *   L(q): Eq. (rhs) of Sec. 3.1 - per direction, conservative-to-primitive
+ *     conversion, WENO5 reconstruction of the primitive variables
+ *     (Sec. 3.2.1 / Sec. 4.2.2), HLLC flux and face velocity (Sec. 3.2.2),
+ *     flux difference plus alpha div(u) for the volume-fraction rows;
+ *   ghost cells: periodic, transmissive (zeroth-order extrapolation) or
+ *     reflective (mirror, normal momentum negated) (Sec. 3.3);
+ *   time step: third-order TVD Runge-Kutta (Sec. 3.4) with
+ *     dt = CFL * min over cells and directions of dx_d / (|u_d| + c).
+ * The adjoint entry points (mfc_rhs_vjp, mfc_rk3_step_vjp) have no
+ * counterpart in the paper: they are the exact transposed derivatives of
+ * mfc_rhs and mfc_rk3_step at fixed dt.
+ *
+ * Memory layout.  Every state-shaped buffer (q, rhs, w, q_bar, ...) is a
+ * DEVICE pointer to float64, structure-of-arrays, C order
+ *     [field][nz + 2g][ny + 2g][nx + 2g]
+ * where g = grid.ghost on each active axis and inactive axes have extent 1
+ * and no ghost layer.  mfc_field_stride() returns the doubles per field.
+ * The library reads and writes interior cells only; ghost entries of caller
+ * buffers are never read and never written (boundary values are produced by
+ * index remapping inside the kernels).
+ *
+ * Ownership.  The caller owns every buffer passed in.  The library owns its
+ * scratch buffers (allocated by mfc_init, and on the first adjoint call for
+ * the adjoint's extra scratch) and frees them in mfc_destroy.
+ *
+ * Execution.  Calls are asynchronous on the given CUDA stream
+ * (a cudaStream_t passed as void*, NULL = legacy default stream) unless a
+ * HOST output pointer is documented, in which case the call synchronises
+ * that stream.  A context may be used by one stream at a time.
+ *
+ * Errors.  Every call returns an mfc_status.  Argument errors are detected
+ * on the host before any launch (MFC_ERR_ARG).  Kernels that meet a
+ * non-physical state (mixture density <= 0, or a squared sound speed <= 0 or
+ * NaN) set a device flag; it is reported as MFC_ERR_NONPHYSICAL (and
+ * cleared) by the next call that synchronises: mfc_compute_dt and
+ * mfc_check.  mfc_last_error() describes the last failure.  No exception
+ * crosses the ABI.
+ */
+#ifndef MFC_H
+#define MFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MFC_OK = 0,
+    MFC_ERR_ARG = -1,          /* invalid argument (checked on the host) */
+    MFC_ERR_ALLOC = -2,        /* device allocation failed */
+    MFC_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
+    MFC_ERR_NONPHYSICAL = -4,  /* rho <= 0 or c^2 <= 0 / NaN met on the device */
+    MFC_ERR_UNSUPPORTED = -5   /* valid but not supported by this build */
+} mfc_status;
+
+typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2 } mfc_bc;
+
+/* MFC_FP64: everything in float64.
+ * MFC_MIXED: WENO5 reconstruction, HLLC and the per-direction flux
+ * difference in float32; conservative-to-primitive conversion, the sum over
+ * directions, the Runge-Kutta stage update and the CFL reduction in float64. */
+typedef enum { MFC_FP64 = 0, MFC_MIXED = 1 } mfc_precision;
+
+/* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2). */
+typedef enum { MFC_WENO_JS = 0, MFC_WENO_M = 1, MFC_WENO_Z = 2 } mfc_weno;
+
+/* Uniform Cartesian grid.  n[d] interior cells on [lo[d], hi[d]] for
+ * d < ndim (n[d] = 1 for d >= ndim).  ghost >= 0 is the padding of the
+ * buffer layout on each active axis (MFC uses 3 for WENO5).  Periodic must
+ * be set on both ends of an axis; periodic and reflective axes need n >= 3. */
+typedef struct {
+    int32_t ndim;          /* 1, 2 or 3 */
+    int64_t n[3];
+    double lo[3], hi[3];
+    int32_t ghost;
+    int32_t bc_lo[3], bc_hi[3];  /* mfc_bc */
+} mfc_grid;
+
+/* Stiffened-gas fluids (Sec. 2.2): gamma_i > 1, pi_inf_i >= 0. */
+typedef struct {
+    int32_t nfluids;       /* 1 .. 4 */
+    double gamma[4];
+    double pi_inf[4];
+} mfc_eos;
+
+typedef struct {
+    int32_t precision;     /* mfc_precision */
+    int32_t weno;          /* mfc_weno */
+    double weno_eps;       /* > 0: epsilon of the nonlinear weights (1e-40 for M and Z, 1e-6 for JS) */
+    double cfl;            /* > 0: Courant number used when a step is asked for dt <= 0 */
+} mfc_opts;
+
+typedef struct mfc_ctx mfc_ctx;
+
+/* Validate the description, derive the constants and allocate the scratch
+ * (three state-sized float64 buffers) on the current CUDA device.
+ * *out receives the context (NULL on failure). */
+mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts, mfc_ctx** out);
+
+/* Free the context and its scratch (synchronises the device first).  NULL is a no-op. */
+mfc_status mfc_destroy(mfc_ctx* ctx);
+
+/* Doubles per field of a state-sized buffer (padded layout), or -1. */
+int64_t mfc_field_stride(const mfc_ctx* ctx);
+
+/* Number of fields N_q = 2 N_f + ndim, or -1. */
+int32_t mfc_num_fields(const mfc_ctx* ctx);
+
+/* Primitive (alpha_i rho_i, u_d, p, alpha_j) -> conservative state:
+ * rho u = rho * u, rho E = Gamma p + Pi + 1/2 rho |u|^2 (Sec. 2.1.1, 2.2). */
+mfc_status mfc_prim_to_cons(mfc_ctx* ctx, const double* w, double* q, void* stream);
+
+/* Conservative -> primitive: p = (rho E - 1/2 rho |u|^2 - Pi)/Gamma. */
+mfc_status mfc_cons_to_prim(mfc_ctx* ctx, const double* q, double* w, void* stream);
+
+/* CFL time step of state q.  dt_out is a HOST pointer; the call synchronises
+ * the stream and returns MFC_ERR_NONPHYSICAL if the flag was set. */
+mfc_status mfc_compute_dt(mfc_ctx* ctx, const double* q, double* dt_out, void* stream);
+
+/* rhs = L(q) on every interior cell (Eq. (rhs)). */
+mfc_status mfc_rhs(mfc_ctx* ctx, const double* q, double* rhs, void* stream);
+
+/* One TVD-RK3 step in place (Sec. 3.4):
+ *   q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
+ *   q <- 1/3 q + 2/3 (q2 + dt L(q2)).
+ * dt > 0 is used as given; dt <= 0 asks for the CFL dt of q, computed on the
+ * device without a host round trip.  dt_used (nullable) is a DEVICE pointer
+ * to one double that receives the dt of this step. */
+mfc_status mfc_rk3_step(mfc_ctx* ctx, double* q, double dt, double* dt_used, void* stream);
+
+/* nsteps RK3 steps in place, each with its own CFL dt (dt <= 0) or the
+ * fixed dt.  dt_log (nullable) is a DEVICE array of nsteps doubles. */
+mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, double* dt_log, void* stream);
+
+/* Adjoint of mfc_rhs: q_bar += (dL/dq)^T rhs_bar, interior cells.  rhs_bar
+ * and q_bar are state-sized device buffers; q_bar must not alias q or
+ * rhs_bar.  Non-smooth points (min/max of wave speeds, the HLLC side, |.|
+ * of WENO-Z) take the derivative of the branch the forward pass takes. */
+mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, double* q_bar, void* stream);
+
+/* Adjoint of one mfc_rk3_step at the fixed dt > 0:
+ * qn_bar = (d q^{n+1} / d q^n)^T qnp1_bar (overwritten, interior cells).
+ * Recomputes the two intermediate stages from q_n.  qn_bar may alias
+ * qnp1_bar; neither may alias q_n. */
+mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const double* qnp1_bar,
+                            double* qn_bar, void* stream);
+
+/* Synchronise the stream; report (and clear) the non-physical-state flag. */
+mfc_status mfc_check(mfc_ctx* ctx, void* stream);
+
+/* Message of the last failure on this context ("" if none).  With a NULL
+ * context: the last mfc_init failure of this thread. */
+const char* mfc_last_error(const mfc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFC_H */

@@ -247,6 +247,15 @@ template <class T> T sound_speed(T rho, T p, T Gamma, T Pi) {
  * g_r(w) = w (d_r + d_r^2 - 3 d_r w + w^2)/(d_r^2 + w (1 - 2 d_r)) and
  * renormalised; Z (Sec. 4.2.2, q = 1), alpha_r = d_r (1 + tau/(beta_r + eps)),
  * tau = |beta_0 - beta_2|.  dbg (optional) receives p[3], beta[3], omega[3]. */
+/* Jiang-Shu smoothness indicators of the three candidate stencils
+ * (Sec. 4.2.2 with k = 3 on a uniform grid); shared by both edges. */
+template <class T> void weno5_beta(const T* f, T* beta) {
+    const T c13 = T(13.0 / 12.0), c14 = T(0.25);
+    beta[0] = c13 * sq(f[0] - T(2.0) * f[1] + f[2]) + c14 * sq(f[0] - T(4.0) * f[1] + T(3.0) * f[2]);
+    beta[1] = c13 * sq(f[1] - T(2.0) * f[2] + f[3]) + c14 * sq(f[1] - f[3]);
+    beta[2] = c13 * sq(f[2] - T(2.0) * f[3] + f[4]) + c14 * sq(T(3.0) * f[2] - T(4.0) * f[3] + f[4]);
+}
+
 template <class T>
 T weno5_edge(const T* f, bool right_edge, int variant, double eps, T* dbg = nullptr) {
     T p[3], beta[3], d[3];
@@ -261,10 +270,7 @@ T weno5_edge(const T* f, bool right_edge, int variant, double eps, T* dbg = null
         p[2] = (T(11.0) * f[2] - T(7.0) * f[3] + T(2.0) * f[4]) / T(6.0);
         d[0] = T(0.3); d[1] = T(0.6); d[2] = T(0.1);
     }
-    const T c13 = T(13.0 / 12.0), c14 = T(0.25);
-    beta[0] = c13 * sq(f[0] - T(2.0) * f[1] + f[2]) + c14 * sq(f[0] - T(4.0) * f[1] + T(3.0) * f[2]);
-    beta[1] = c13 * sq(f[1] - T(2.0) * f[2] + f[3]) + c14 * sq(f[1] - f[3]);
-    beta[2] = c13 * sq(f[2] - T(2.0) * f[3] + f[4]) + c14 * sq(T(3.0) * f[2] - T(4.0) * f[3] + f[4]);
+    weno5_beta(f, beta);
 
     T a[3], w[3];
     if (variant == WENO_Z) {
@@ -807,8 +813,9 @@ int oc_rk3_step_count(const oc_problem* P, const double* q, double dt, int64_t* 
  * the left and qb as the right primitive state after conversion):
  * row 0 cons_to_prim, row 1 one WENO5 edge value, row 2 HLLC, row 3 the cell
  * term of one direction, row 4 one RK3 stage update of one cell (the costlier
- * stage form a*qn + b*(q + dt*L)), row 5 the CFL quantity of one cell.
- * out: 6 rows x 5 counts. */
+ * stage form a*qn + b*(q + dt*L)), row 5 the CFL quantity of one cell,
+ * row 6 the smoothness indicators of one five-cell stencil (shared by the
+ * two edge values of a cell).  out: 7 rows x 5 counts. */
 int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int64_t* out) {
     if (check_problem(P)) return -1;
     Lay L{P->nf, P->ndim};
@@ -848,6 +855,9 @@ int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int
         }
     }
     take(5);
+    Cnt bt[3];
+    weno5_beta(f, bt);
+    take(6);
     return 0;
 }
 

@@ -1,0 +1,401 @@
+// Reverse-mode (adjoint) building blocks: the exact transposed derivatives
+// of cons_to_prim, weno5_cell and hllc in mfc_device.cuh.  Every function
+// recomputes the forward quantities it needs from its inputs and takes the
+// same branches as the forward code (ties of min / max keep the left
+// argument; d|x|/dx = +1 at 0), so the result is the derivative of the
+// branch the forward pass takes.
+#pragma once
+
+#include "mfc_device.cuh"
+
+namespace mfc {
+
+// q_bar += (dW/dq)^T W_bar for the conservative state q of one cell.
+template <int NF, int ND>
+__device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* wbar, const Consts& C,
+                                                 double* qbar) {
+    using L = Lay<NF, ND>;
+    double rho = q[0];
+#pragma unroll
+    for (int i = 1; i < NF; ++i) rho = rho + q[i];
+    double u[ND];
+    double u2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        u[d] = q[L::MOM + d] / rho;
+        u2 = u2 + u[d] * u[d];
+    }
+    double Gamma, Pi;
+    mixture<NF, double>(q + L::A, C, Gamma, Pi);
+    const double ke = 0.5 * rho * u2;
+    const double p = (q[L::E] - ke - Pi) / Gamma;
+    // p = (E - ke - Pi) / Gamma
+    const double pb = wbar[L::E];
+    const double numb = pb / Gamma;
+    const double Gb = -pb * p / Gamma;
+    const double Pb = -numb;
+    qbar[L::E] += numb;
+    const double keb = -numb;
+    double rhob = keb * 0.5 * u2;
+    const double u2b = keb * 0.5 * rho;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        const double ub = wbar[L::MOM + d] + u2b * 2.0 * u[d];
+        qbar[L::MOM + d] += ub / rho;
+        rhob -= ub * u[d] / rho;
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) qbar[i] += wbar[i] + rhob;
+#pragma unroll
+    for (int j = 0; j < NF - 1; ++j)
+        qbar[L::A + j] += wbar[L::A + j] + Gb * (C.g[j] - C.g[NF - 1]) + Pb * (C.h[j] - C.h[NF - 1]);
+}
+
+// Adjoint of the nonlinear weights and the final sum of one edge:
+// given p[3], beta[3], ideal weights d[3] and out_bar, add to p_bar and
+// beta_bar.
+template <class R>
+__device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const R* d, int variant, R eps, R outb,
+                                               R* pb, R* betab) {
+    R a[3], w[3], t[3];
+    R tau = R(0);
+    if (variant == WENO_Z) {
+        tau = fabs(beta[0] - beta[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a[r] = d[r] * (R(1) + tau / (beta[r] + eps));
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            t[r] = eps + beta[r];
+            a[r] = d[r] / (t[r] * t[r]);
+        }
+    }
+    const R s = a[0] + a[1] + a[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) w[r] = a[r] / s;
+    R om[3], Nn[3], Dd[3], gm[3], sm = R(1);
+    if (variant == WENO_M) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            Nn[r] = d[r] + d[r] * d[r] - R(3) * d[r] * w[r] + w[r] * w[r];
+            Dd[r] = d[r] * d[r] + w[r] * (R(1) - R(2) * d[r]);
+            gm[r] = w[r] * Nn[r] / Dd[r];
+        }
+        sm = gm[0] + gm[1] + gm[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) om[r] = gm[r] / sm;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) om[r] = w[r];
+    }
+    // out = sum om_r p_r
+    R omb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        pb[r] += om[r] * outb;
+        omb[r] = p[r] * outb;
+    }
+    R wb[3];
+    if (variant == WENO_M) {
+        // om_r = gm_r / sm
+        const R dot = omb[0] * om[0] + omb[1] * om[1] + omb[2] * om[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const R gb = (omb[r] - dot) / sm;
+            // gm = w N(w) / D(w), N' = -3 d + 2 w, D' = 1 - 2 d
+            const R dN = R(-3) * d[r] + R(2) * w[r];
+            const R dD = R(1) - R(2) * d[r];
+            const R dg = (Nn[r] + w[r] * dN) / Dd[r] - w[r] * Nn[r] * dD / (Dd[r] * Dd[r]);
+            wb[r] = gb * dg;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) wb[r] = omb[r];
+    }
+    // w_r = a_r / s
+    const R dotw = wb[0] * w[0] + wb[1] * w[1] + wb[2] * w[2];
+    R ab[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ab[r] = (wb[r] - dotw) / s;
+    if (variant == WENO_Z) {
+        R taub = R(0);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const R be = beta[r] + eps;
+            taub += ab[r] * d[r] / be;
+            betab[r] += -ab[r] * d[r] * tau / (be * be);
+        }
+        const R sg = (beta[0] - beta[2] >= R(0)) ? R(1) : R(-1);
+        betab[0] += taub * sg;
+        betab[2] -= taub * sg;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) betab[r] += ab[r] * (R(-2) * a[r] / t[r]);
+    }
+}
+
+// Adjoint of weno5_cell: given the bars of the right-edge value (vrb) and
+// the left-edge value (vlb), add df to fb[0..4].
+template <class R>
+__device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R* fb) {
+    const R c13 = R(13.0 / 12.0), c14 = R(0.25);
+    const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
+    const R A1 = f[1] - R(2) * f[2] + f[3], B1 = f[1] - f[3];
+    const R A2 = f[2] - R(2) * f[3] + f[4], B2 = R(3) * f[2] - R(4) * f[3] + f[4];
+    R beta[3];
+    beta[0] = c13 * (A0 * A0) + c14 * (B0 * B0);
+    beta[1] = c13 * (A1 * A1) + c14 * (B1 * B1);
+    beta[2] = c13 * (A2 * A2) + c14 * (B2 * B2);
+    R betab[3] = {R(0), R(0), R(0)};
+    const R sixth = R(1) / R(6);
+    if (vrb != R(0)) {
+        R p[3], pb[3] = {R(0), R(0), R(0)};
+        const R d[3] = {R(0.1), R(0.6), R(0.3)};
+        p[0] = (R(2) * f[0] - R(7) * f[1] + R(11) * f[2]) / R(6);
+        p[1] = (-f[1] + R(5) * f[2] + R(2) * f[3]) / R(6);
+        p[2] = (R(2) * f[2] + R(5) * f[3] - f[4]) / R(6);
+        weno5_edge_adj(p, beta, d, variant, eps, vrb, pb, betab);
+        fb[0] += (R(2) * pb[0]) * sixth;
+        fb[1] += (R(-7) * pb[0] - pb[1]) * sixth;
+        fb[2] += (R(11) * pb[0] + R(5) * pb[1] + R(2) * pb[2]) * sixth;
+        fb[3] += (R(2) * pb[1] + R(5) * pb[2]) * sixth;
+        fb[4] += (-pb[2]) * sixth;
+    }
+    if (vlb != R(0)) {
+        R p[3], pb[3] = {R(0), R(0), R(0)};
+        const R d[3] = {R(0.3), R(0.6), R(0.1)};
+        p[0] = (-f[0] + R(5) * f[1] + R(2) * f[2]) / R(6);
+        p[1] = (R(2) * f[1] + R(5) * f[2] - f[3]) / R(6);
+        p[2] = (R(11) * f[2] - R(7) * f[3] + R(2) * f[4]) / R(6);
+        weno5_edge_adj(p, beta, d, variant, eps, vlb, pb, betab);
+        fb[0] += (-pb[0]) * sixth;
+        fb[1] += (R(5) * pb[0] + R(2) * pb[1]) * sixth;
+        fb[2] += (R(2) * pb[0] + R(5) * pb[1] + R(11) * pb[2]) * sixth;
+        fb[3] += (-pb[1] - R(7) * pb[2]) * sixth;
+        fb[4] += (R(2) * pb[2]) * sixth;
+    }
+    // beta_r = c13 A_r^2 + c14 B_r^2
+    const R a0 = R(2) * c13 * A0 * betab[0], b0 = R(2) * c14 * B0 * betab[0];
+    const R a1 = R(2) * c13 * A1 * betab[1], b1 = R(2) * c14 * B1 * betab[1];
+    const R a2 = R(2) * c13 * A2 * betab[2], b2 = R(2) * c14 * B2 * betab[2];
+    fb[0] += a0 + b0;
+    fb[1] += R(-2) * a0 - R(4) * b0 + a1 + b1;
+    fb[2] += a0 + R(3) * b0 + R(-2) * a1 + a2 + R(3) * b2;
+    fb[3] += a1 - b1 + R(-2) * a2 - R(4) * b2;
+    fb[4] += a2 + b2;
+}
+
+// Adjoint of hllc: given F_bar[NQ] and uf_bar, add to WLb, WRb.
+// Also returns the forward face velocity in uf_out.
+template <int NF, int ND, int DIR, class R>
+__device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts& C, const R* Fb, R ufb, R* WLb,
+                                         R* WRb, R& uf_out) {
+    using L = Lay<NF, ND>;
+    constexpr int NQ = L::NQ;
+    // ---- forward recomputation ----
+    R rho[2], un[2], p[2], E[2], c[2], G[2], P[2], u2[2], c2[2];
+#pragma unroll
+    for (int K = 0; K < 2; ++K) {
+        const R* w = K ? WR : WL;
+        R r = w[0];
+#pragma unroll
+        for (int i = 1; i < NF; ++i) r = r + w[i];
+        R s2 = R(0);
+#pragma unroll
+        for (int e = 0; e < ND; ++e) s2 = s2 + w[L::MOM + e] * w[L::MOM + e];
+        mixture<NF, R>(w + L::A, C, G[K], P[K]);
+        rho[K] = r;
+        u2[K] = s2;
+        un[K] = w[L::MOM + DIR];
+        p[K] = w[L::E];
+        E[K] = G[K] * p[K] + P[K] + R(0.5) * r * s2;
+        c2[K] = ((G[K] + R(1)) * p[K] + P[K]) / (G[K] * r);
+        c[K] = sqrt(c2[K]);
+    }
+    const R aL = un[0] - c[0], aR = un[1] - c[1];
+    const bool minR = aR < aL;
+    const R SL = minR ? aR : aL;
+    const R bL = un[0] + c[0], bR = un[1] + c[1];
+    const bool maxR = bR > bL;
+    const R SR = maxR ? bR : bL;
+    const R num = p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]);
+    const R den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
+    const R Ss = num / den;
+    const bool left = Ss >= R(0);
+    const int K = left ? 0 : 1;
+    const R* w = left ? WL : WR;
+    const R rK = rho[K], uK = un[K], pK = p[K], EK = E[K];
+    const R SK = left ? SL : SR;
+    const bool star = left ? (SL < R(0)) : (SR > R(0));
+    const R uf = star ? Ss : uK;
+    uf_out = uf;
+
+    // ---- reverse ----
+    R wb[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) wb[k] = R(0);
+    R rKb = R(0), uKb = R(0), pKb = R(0), EKb = R(0), SKb = R(0), Ssb = R(0);
+    R ufb_t = ufb;
+    // alpha slots: F = alpha_K uf
+#pragma unroll
+    for (int j = 0; j < NF - 1; ++j) {
+        wb[L::A + j] += Fb[L::A + j] * uf;
+        ufb_t += Fb[L::A + j] * w[L::A + j];
+    }
+    if (star) {
+        Ssb += ufb_t;
+        const R A = SK - uK, B = SK - Ss;
+        const R chi = A / B;
+        R chib = R(0);
+        // energy
+        const R Z = rK * (SK - uK);
+        const R Y = Ss + pK / Z;
+        const R X = EK / rK + (Ss - uK) * Y;
+        const R Es = chi * rK * X;
+        SKb += Fb[L::E] * (Es - EK);
+        const R Esb = Fb[L::E] * SK;
+        EKb -= Fb[L::E] * SK;
+        chib += Esb * rK * X;
+        rKb += Esb * chi * X;
+        const R Xb = Esb * chi * rK;
+        EKb += Xb / rK;
+        rKb -= Xb * EK / (rK * rK);
+        Ssb += Xb * Y;
+        uKb -= Xb * Y;
+        const R Yb = Xb * (Ss - uK);
+        Ssb += Yb;
+        pKb += Yb / Z;
+        const R Zb = -Yb * pK / (Z * Z);
+        rKb += Zb * (SK - uK);
+        SKb += Zb * rK;
+        uKb -= Zb * rK;
+        // momentum
+#pragma unroll
+        for (int e = 0; e < ND; ++e) {
+            const R Fe = Fb[L::MOM + e];
+            const R we = w[L::MOM + e];
+            const R ve = (e == DIR) ? Ss : we;
+            SKb += Fe * (chi * rK * ve - rK * we);
+            chib += Fe * SK * rK * ve;
+            rKb += Fe * SK * (chi * ve - we);
+            if (e == DIR) {
+                Ssb += Fe * SK * chi * rK;
+                wb[L::MOM + e] -= Fe * SK * rK;
+            } else {
+                wb[L::MOM + e] += Fe * SK * rK * (chi - R(1));
+            }
+        }
+        // partial densities
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {
+            SKb += Fb[i] * (chi - R(1)) * w[i];
+            chib += Fb[i] * SK * w[i];
+            wb[i] += Fb[i] * SK * (chi - R(1));
+        }
+        // chi = A / B
+        const R Ab = chib / B;
+        const R Bb = -chib * chi / B;
+        SKb += Ab + Bb;
+        uKb -= Ab;
+        Ssb -= Bb;
+    } else {
+        uKb += ufb_t;
+    }
+    // physical flux of side K
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        wb[i] += Fb[i] * uK;
+        uKb += Fb[i] * w[i];
+    }
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+        const R Fe = Fb[L::MOM + e];
+        rKb += Fe * uK * w[L::MOM + e];
+        uKb += Fe * rK * w[L::MOM + e];
+        wb[L::MOM + e] += Fe * rK * uK;
+        if (e == DIR) pKb += Fe;
+    }
+    EKb += Fb[L::E] * uK;
+    pKb += Fb[L::E] * uK;
+    uKb += Fb[L::E] * (EK + pK);
+
+    // per-side bars
+    R rb[2] = {R(0), R(0)}, unb[2] = {R(0), R(0)}, pb[2] = {R(0), R(0)}, Eb[2] = {R(0), R(0)},
+      cb[2] = {R(0), R(0)};
+    rb[K] += rKb;
+    unb[K] += uKb;
+    pb[K] += pKb;
+    Eb[K] += EKb;
+    R SLb = left ? SKb : R(0);
+    R SRb = left ? R(0) : SKb;
+    // Ss = num / den
+    const R numb = Ssb / den;
+    const R denb = -Ssb * Ss / den;
+    pb[1] += numb;
+    pb[0] -= numb;
+    rb[0] += numb * un[0] * (SL - un[0]);
+    unb[0] += numb * rho[0] * (SL - R(2) * un[0]);
+    SLb += numb * rho[0] * un[0];
+    rb[1] -= numb * un[1] * (SR - un[1]);
+    unb[1] -= numb * rho[1] * (SR - R(2) * un[1]);
+    SRb -= numb * rho[1] * un[1];
+    rb[0] += denb * (SL - un[0]);
+    SLb += denb * rho[0];
+    unb[0] -= denb * rho[0];
+    rb[1] -= denb * (SR - un[1]);
+    SRb -= denb * rho[1];
+    unb[1] += denb * rho[1];
+    // wave speeds
+    if (minR) {
+        unb[1] += SLb;
+        cb[1] -= SLb;
+    } else {
+        unb[0] += SLb;
+        cb[0] -= SLb;
+    }
+    if (maxR) {
+        unb[1] += SRb;
+        cb[1] += SRb;
+    } else {
+        unb[0] += SRb;
+        cb[0] += SRb;
+    }
+    // merge the side-K primitive bars collected in wb
+    R* outs[2] = {WLb, WRb};
+    {
+        R* o = outs[K];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) o[k] += wb[k];
+    }
+#pragma unroll
+    for (int S = 0; S < 2; ++S) {
+        const R* ws = S ? WR : WL;
+        R* o = outs[S];
+        // c = sqrt(c2), c2 = ((G + 1) p + P) / (G r)
+        const R c2b = cb[S] / (R(2) * c[S]);
+        const R Dd = G[S] * rho[S];
+        const R Nnb = c2b / Dd;
+        const R Ddb = -c2b * c2[S] / Dd;
+        R Gb = Nnb * p[S] + Ddb * rho[S];
+        R Pb = Nnb;
+        R pbs = pb[S] + Nnb * (G[S] + R(1));
+        R rbs = rb[S] + Ddb * G[S];
+        // E = G p + P + 0.5 r u2
+        Gb += Eb[S] * p[S];
+        pbs += Eb[S] * G[S];
+        Pb += Eb[S];
+        rbs += Eb[S] * R(0.5) * u2[S];
+        const R u2b = Eb[S] * R(0.5) * rho[S];
+#pragma unroll
+        for (int e = 0; e < ND; ++e) o[L::MOM + e] += u2b * R(2) * ws[L::MOM + e];
+        o[L::MOM + DIR] += unb[S];
+        o[L::E] += pbs;
+#pragma unroll
+        for (int i = 0; i < NF; ++i) o[i] += rbs;
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j)
+            o[L::A + j] += Gb * (coef_g<R>(C, j) - coef_g<R>(C, NF - 1)) + Pb * (coef_h<R>(C, j) - coef_h<R>(C, NF - 1));
+    }
+}
+
+}  // namespace mfc

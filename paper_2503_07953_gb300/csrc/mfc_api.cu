@@ -1,0 +1,478 @@
+// C ABI of the library (declared in include/mfc.h): argument checking,
+// scratch ownership and the launch sequences of L(q), the RK3 step and the
+// adjoints.  All numerical work runs in the kernels of mfc_fwd.cuh and
+// mfc_vjp.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/mfc.h"
+#include "mfc_launch.h"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DevScalars {
+    unsigned long long minbits;  // CFL minimum (bit pattern of a positive double)
+    double dt;                   // dt of the current step
+    int flag;                    // non-physical state seen
+    int pad;
+};
+
+}  // namespace
+
+struct mfc_ctx {
+    mfc_grid grid;
+    mfc_eos eos;
+    mfc_opts opts;
+    mfc::Consts C;
+    const mfc::LaunchFns* fns;
+    int device;
+    int64_t total;        // doubles in a state-sized buffer
+    double* q1 = nullptr;  // RK stage 1
+    double* q2 = nullptr;  // RK stage 2
+    double* r = nullptr;   // accumulated right-hand side
+    // adjoint scratch (allocated on first use)
+    double* a1 = nullptr;
+    double* a2 = nullptr;
+    double* a3 = nullptr;
+    DevScalars* scal = nullptr;
+    std::string err;
+};
+
+namespace mfc {
+
+int sweep_segment(int64_t n, int64_t nlines) {
+    // Aim for ~8 resident 128-thread blocks per SM on 152 SMs; longer
+    // segments amortise the 6-cell halo, shorter ones fill the GPU.
+    const int64_t target = 152LL * 1024;
+    int64_t seg = (n * nlines + target - 1) / target;
+    if (seg < 16) seg = 16;
+    if (seg > 64) seg = 64;
+    if (seg > n) seg = n;
+    if (seg < 1) seg = 1;
+    return (int)seg;
+}
+
+}  // namespace mfc
+
+namespace {
+
+__global__ void set_scalars_kernel(DevScalars* s, double dt) {
+    s->minbits = 0x7ff0000000000000ULL;  // +inf
+    s->dt = dt;
+}
+
+__global__ void finalize_dt_kernel(DevScalars* s, double cfl, double* dt_out) {
+    const double m = __longlong_as_double((long long)s->minbits);
+    s->dt = cfl * m;
+    if (dt_out) *dt_out = s->dt;
+}
+
+__global__ void copy_dt_kernel(const DevScalars* s, double* dt_out) { *dt_out = s->dt; }
+
+// out = a x + b y + c z on the interior cells of every field (y, z may be
+// null when their coefficient is 0).  Element-wise, so out may alias x, y or z.
+__global__ void lincomb_kernel(const mfc::Consts C, double* out, double a, const double* x, double b,
+                               const double* y, double c, const double* z) {
+    const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
+    const int64_t total = ncell * C.nq;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = t / ncell, lin = t - f * ncell;
+        const int64_t i = lin % C.n[0];
+        const int64_t j = (lin / C.n[0]) % C.n[1];
+        const int64_t k = lin / (C.n[0] * C.n[1]);
+        const int64_t o = C.origin + i * C.stride[0] + j * C.stride[1] + k * C.stride[2] + f * C.fstride;
+        double v = a * x[o];
+        if (y) v += b * y[o];
+        if (z) v += c * z[o];
+        out[o] = v;
+    }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mfc_status fail(mfc_ctx* ctx, mfc_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+mfc_status cuda_fail(mfc_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, MFC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o) {
+    if (!g || !e || !o) return "null description pointer";
+    if (g->ndim < 1 || g->ndim > 3) return "ndim must be 1, 2 or 3";
+    if (g->ghost < 0 || g->ghost > 64) return "ghost must be in [0, 64]";
+    for (int a = 0; a < 3; ++a) {
+        if (a < g->ndim) {
+            if (g->n[a] < 1) return "every active axis needs n >= 1";
+            if (!(g->hi[a] > g->lo[a]) || !std::isfinite(g->hi[a] - g->lo[a])) return "need lo < hi on active axes";
+            for (int s = 0; s < 2; ++s) {
+                const int bc = s ? g->bc_hi[a] : g->bc_lo[a];
+                if (bc < 0 || bc > 2) return "unknown boundary condition";
+                if (bc != MFC_BC_TRANSMISSIVE && g->n[a] < 3) return "periodic / reflective axes need n >= 3";
+            }
+            if ((g->bc_lo[a] == MFC_BC_PERIODIC) != (g->bc_hi[a] == MFC_BC_PERIODIC))
+                return "periodic must be set on both ends of an axis";
+        } else if (g->n[a] != 1) {
+            return "inactive axes must have n = 1";
+        }
+    }
+    const double cells = (double)g->n[0] * (double)g->n[1] * (double)g->n[2];
+    if (cells > 4.0e12) return "grid too large";
+    if (e->nfluids < 1 || e->nfluids > 4) return "nfluids must be 1 .. 4";
+    for (int i = 0; i < e->nfluids; ++i) {
+        if (!(e->gamma[i] > 1.0) || !std::isfinite(e->gamma[i])) return "gamma must be > 1";
+        if (!(e->pi_inf[i] >= 0.0) || !std::isfinite(e->pi_inf[i])) return "pi_inf must be >= 0";
+    }
+    if (o->precision != MFC_FP64 && o->precision != MFC_MIXED) return "unknown precision";
+    if (o->weno < 0 || o->weno > 2) return "unknown WENO variant";
+    if (!(o->weno_eps > 0.0) || !std::isfinite(o->weno_eps)) return "weno_eps must be > 0";
+    if (!(o->cfl > 0.0) || !std::isfinite(o->cfl)) return "cfl must be > 0";
+    return "";
+}
+
+void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Consts& C, int64_t& total) {
+    std::memset(&C, 0, sizeof(C));
+    C.nf = e->nfluids;
+    C.nd = g->ndim;
+    C.nq = 2 * C.nf + C.nd;
+    C.weno = o->weno;
+    int64_t np[3];
+    for (int a = 0; a < 3; ++a) {
+        C.n[a] = g->n[a];
+        np[a] = g->n[a] + (a < g->ndim ? 2 * (int64_t)g->ghost : 0);
+        C.bc_lo[a] = a < g->ndim ? g->bc_lo[a] : MFC_BC_TRANSMISSIVE;
+        C.bc_hi[a] = a < g->ndim ? g->bc_hi[a] : MFC_BC_TRANSMISSIVE;
+        C.dx[a] = a < g->ndim ? (g->hi[a] - g->lo[a]) / (double)g->n[a] : 1.0;
+        C.inv_dx[a] = 1.0 / C.dx[a];
+        C.inv_dxf[a] = (float)C.inv_dx[a];
+    }
+    C.stride[0] = 1;
+    C.stride[1] = np[0];
+    C.stride[2] = np[0] * np[1];
+    C.fstride = np[0] * np[1] * np[2];
+    C.origin = 0;
+    for (int a = 0; a < g->ndim; ++a) C.origin += (int64_t)g->ghost * C.stride[a];
+    for (int i = 0; i < e->nfluids; ++i) {
+        C.g[i] = 1.0 / (e->gamma[i] - 1.0);
+        C.h[i] = e->gamma[i] * e->pi_inf[i] / (e->gamma[i] - 1.0);
+        C.gf[i] = (float)C.g[i];
+        C.hf[i] = (float)C.h[i];
+    }
+    C.eps = o->weno_eps;
+    // float32 WENO: (eps + beta)^2 must stay a normal float when beta = 0
+    C.epsf = (float)(o->weno_eps < 1e-18 ? 1e-18 : o->weno_eps);
+    C.cfl = o->cfl;
+    total = C.fstride * C.nq;
+}
+
+const mfc::LaunchFns* fns_for(int nf) {
+    switch (nf) {
+        case 1: return &mfc::launch_fns_nf1();
+        case 2: return &mfc::launch_fns_nf2();
+        case 3: return &mfc::launch_fns_nf3();
+        default: return &mfc::launch_fns_nf4();
+    }
+}
+
+// dt into ctx->scal->dt: the given value, or the CFL dt of q.
+mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
+    cudaError_t e;
+    set_scalars_kernel<<<1, 1, 0, s>>>(ctx->scal, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "set scalars");
+    if (dt > 0.0) return MFC_OK;
+    if ((e = ctx->fns->cfl(ctx->C, q, &ctx->scal->minbits, &ctx->scal->flag, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cfl kernel");
+    finalize_dt_kernel<<<1, 1, 0, s>>>(ctx->scal, ctx->C.cfl, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "finalize dt");
+    return MFC_OK;
+}
+
+// All directional sweeps of one evaluation of L(qin).  out_kind 0 writes
+// L into rhs; 1 and 2 fuse the RK stage update into the last sweep.
+mfc_status eval_L(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, const double* qn, double* qout,
+                  double a, double b, cudaStream_t s) {
+    for (int d = 0; d < ctx->C.nd; ++d) {
+        mfc::SweepArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.q = qin;
+        A.rhs = rhs;
+        A.acc_in = d > 0;
+        const bool last = d == ctx->C.nd - 1;
+        A.out_kind = last ? out_kind : 0;
+        A.qn = qn;
+        A.qout = qout;
+        A.dt = &ctx->scal->dt;
+        A.rk_a = a;
+        A.rk_b = b;
+        A.flag = &ctx->scal->flag;
+        cudaError_t e = ctx->fns->sweep(ctx->C, d, ctx->opts.precision, A, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep kernel");
+    }
+    return MFC_OK;
+}
+
+const double RK_A2 = 0.75, RK_B2 = 0.25, RK_A3 = 1.0 / 3.0, RK_B3 = 2.0 / 3.0;
+
+mfc_status rk3_once(mfc_ctx* ctx, double* q, double dt, double* dt_used, cudaStream_t s) {
+    mfc_status st = eval_dt(ctx, q, dt, s);
+    if (st != MFC_OK) return st;
+    if ((st = eval_L(ctx, q, ctx->r, 1, nullptr, ctx->q1, 0.0, 1.0, s)) != MFC_OK) return st;
+    if ((st = eval_L(ctx, ctx->q1, ctx->r, 2, q, ctx->q2, RK_A2, RK_B2, s)) != MFC_OK) return st;
+    if ((st = eval_L(ctx, ctx->q2, ctx->r, 2, q, q, RK_A3, RK_B3, s)) != MFC_OK) return st;
+    if (dt_used) {
+        copy_dt_kernel<<<1, 1, 0, s>>>(ctx->scal, dt_used);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy dt");
+    }
+    return MFC_OK;
+}
+
+mfc_status lincomb(mfc_ctx* ctx, double* out, double a, const double* x, double b, const double* y, double c,
+                   const double* z, cudaStream_t s) {
+    const int64_t total = ctx->C.n[0] * ctx->C.n[1] * ctx->C.n[2] * ctx->C.nq;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    lincomb_kernel<<<(unsigned)blocks, 256, 0, s>>>(ctx->C, out, a, x, b, y, c, z);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "lincomb kernel");
+}
+
+// qbar += (dL/dq)^T rbar: one adjoint sweep per direction.
+mfc_status eval_L_vjp(mfc_ctx* ctx, const double* q, const double* rbar, double* qbar, cudaStream_t s) {
+    for (int d = 0; d < ctx->C.nd; ++d) {
+        mfc::VjpArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.q = q;
+        A.rbar = rbar;
+        A.qbar = qbar;
+        cudaError_t e = ctx->fns->sweep_vjp(ctx->C, d, ctx->opts.precision, A, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint sweep kernel");
+    }
+    return MFC_OK;
+}
+
+mfc_status ensure_adjoint_scratch(mfc_ctx* ctx) {
+    if (ctx->a1) return MFC_OK;
+    const size_t bytes = (size_t)ctx->total * sizeof(double);
+    if (cudaMalloc(&ctx->a1, bytes) != cudaSuccess || cudaMalloc(&ctx->a2, bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->a3, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        for (double** p : {&ctx->a1, &ctx->a2, &ctx->a3}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        return fail(ctx, MFC_ERR_ALLOC, "device allocation of the adjoint scratch failed");
+    }
+    return MFC_OK;
+}
+
+mfc_status read_flag(mfc_ctx* ctx, cudaStream_t s) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, &ctx->scal->flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read flag");
+    if (flag) {
+        e = cudaMemsetAsync(&ctx->scal->flag, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "clear flag");
+        return fail(ctx, MFC_ERR_NONPHYSICAL, "non-physical state (rho <= 0 or c^2 <= 0) met on the device");
+    }
+    return MFC_OK;
+}
+
+#define MFC_CHECK_CTX(ctx)                  \
+    do {                                    \
+        if (!(ctx)) return MFC_ERR_ARG;     \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts, mfc_ctx** out) {
+    if (!out) {
+        g_init_error = "null output pointer";
+        return MFC_ERR_ARG;
+    }
+    *out = nullptr;
+    const std::string why = check_description(grid, eos, opts);
+    if (!why.empty()) {
+        g_init_error = why;
+        return MFC_ERR_ARG;
+    }
+    mfc_ctx* ctx = new (std::nothrow) mfc_ctx();
+    if (!ctx) {
+        g_init_error = "host allocation failed";
+        return MFC_ERR_ALLOC;
+    }
+    ctx->grid = *grid;
+    ctx->eos = *eos;
+    ctx->opts = *opts;
+    make_consts(grid, eos, opts, ctx->C, ctx->total);
+    ctx->fns = fns_for(eos->nfluids);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        delete ctx;
+        return MFC_ERR_CUDA;
+    }
+    const size_t bytes = (size_t)ctx->total * sizeof(double);
+    if (cudaMalloc(&ctx->q1, bytes) != cudaSuccess || cudaMalloc(&ctx->q2, bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->r, bytes) != cudaSuccess || cudaMalloc(&ctx->scal, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        g_init_error = "device allocation of the scratch buffers failed";
+        mfc_destroy(ctx);
+        return MFC_ERR_ALLOC;
+    }
+    if ((e = cudaMemset(ctx->scal, 0, sizeof(DevScalars))) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        g_init_error = std::string("initialising scalars: ") + cudaGetErrorString(e);
+        mfc_destroy(ctx);
+        return MFC_ERR_CUDA;
+    }
+    g_init_error.clear();
+    *out = ctx;
+    return MFC_OK;
+}
+
+mfc_status mfc_destroy(mfc_ctx* ctx) {
+    if (!ctx) return MFC_OK;
+    DeviceGuard guard(ctx->device);
+    cudaDeviceSynchronize();
+    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3})
+        if (p) cudaFree(p);
+    if (ctx->scal) cudaFree(ctx->scal);
+    delete ctx;
+    return MFC_OK;
+}
+
+int64_t mfc_field_stride(const mfc_ctx* ctx) { return ctx ? ctx->C.fstride : -1; }
+
+int32_t mfc_num_fields(const mfc_ctx* ctx) { return ctx ? ctx->C.nq : -1; }
+
+mfc_status mfc_prim_to_cons(mfc_ctx* ctx, const double* w, double* q, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!w || !q) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = ctx->fns->prim_to_cons(ctx->C, w, q, (cudaStream_t)stream);
+    return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "prim_to_cons");
+}
+
+mfc_status mfc_cons_to_prim(mfc_ctx* ctx, const double* q, double* w, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!w || !q) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = ctx->fns->cons_to_prim(ctx->C, q, w, &ctx->scal->flag, (cudaStream_t)stream);
+    return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "cons_to_prim");
+}
+
+mfc_status mfc_compute_dt(mfc_ctx* ctx, const double* q, double* dt_out, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q || !dt_out) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mfc_status st = eval_dt(ctx, q, 0.0, s);
+    if (st != MFC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(dt_out, &ctx->scal->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy dt");
+    return read_flag(ctx, s);
+}
+
+mfc_status mfc_rhs(mfc_ctx* ctx, const double* q, double* rhs, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q || !rhs) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    if (q == rhs) return fail(ctx, MFC_ERR_ARG, "rhs must not alias q");
+    DeviceGuard guard(ctx->device);
+    return eval_L(ctx, q, rhs, 0, nullptr, nullptr, 0.0, 0.0, (cudaStream_t)stream);
+}
+
+mfc_status mfc_rk3_step(mfc_ctx* ctx, double* q, double dt, double* dt_used, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    if (!std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "dt must be finite");
+    DeviceGuard guard(ctx->device);
+    return rk3_once(ctx, q, dt, dt_used, (cudaStream_t)stream);
+}
+
+mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, double* dt_log, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q || nsteps < 0) return fail(ctx, MFC_ERR_ARG, "null buffer or negative step count");
+    if (!std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "dt must be finite");
+    DeviceGuard guard(ctx->device);
+    for (int32_t i = 0; i < nsteps; ++i) {
+        mfc_status st = rk3_once(ctx, q, dt, dt_log ? dt_log + i : nullptr, (cudaStream_t)stream);
+        if (st != MFC_OK) return st;
+    }
+    return MFC_OK;
+}
+
+mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, double* q_bar, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q || !rhs_bar || !q_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    if (q_bar == q || q_bar == rhs_bar) return fail(ctx, MFC_ERR_ARG, "q_bar must not alias q or rhs_bar");
+    DeviceGuard guard(ctx->device);
+    return eval_L_vjp(ctx, q, rhs_bar, q_bar, (cudaStream_t)stream);
+}
+
+mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const double* qnp1_bar, double* qn_bar,
+                            void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (!q_n || !qnp1_bar || !qn_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "the adjoint needs the step's dt > 0");
+    if (qn_bar == q_n || qnp1_bar == q_n) return fail(ctx, MFC_ERR_ARG, "bars must not alias q_n");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mfc_status st = ensure_adjoint_scratch(ctx);
+    if (st != MFC_OK) return st;
+    // recompute the stages q1, q2 of the forward step at the same dt
+    if ((st = eval_dt(ctx, q_n, dt, s)) != MFC_OK) return st;
+    if ((st = eval_L(ctx, q_n, ctx->r, 1, nullptr, ctx->q1, 0.0, 1.0, s)) != MFC_OK) return st;
+    if ((st = eval_L(ctx, ctx->q1, ctx->r, 2, q_n, ctx->q2, RK_A2, RK_B2, s)) != MFC_OK) return st;
+    const double* g3 = qnp1_bar;
+    double *b2 = ctx->a1, *r = ctx->a2, *b1 = ctx->a3;
+    // q^{n+1} = 1/3 q^n + 2/3 (q2 + dt L(q2))
+    if ((st = lincomb(ctx, b2, RK_B3, g3, 0.0, nullptr, 0.0, nullptr, s)) != MFC_OK) return st;
+    if ((st = lincomb(ctx, r, RK_B3 * dt, g3, 0.0, nullptr, 0.0, nullptr, s)) != MFC_OK) return st;
+    if ((st = eval_L_vjp(ctx, ctx->q2, r, b2, s)) != MFC_OK) return st;
+    // q2 = 3/4 q^n + 1/4 (q1 + dt L(q1))
+    if ((st = lincomb(ctx, b1, RK_B2, b2, 0.0, nullptr, 0.0, nullptr, s)) != MFC_OK) return st;
+    if ((st = lincomb(ctx, r, RK_B2 * dt, b2, 0.0, nullptr, 0.0, nullptr, s)) != MFC_OK) return st;
+    if ((st = eval_L_vjp(ctx, ctx->q1, r, b1, s)) != MFC_OK) return st;
+    // q1 = q^n + dt L(q^n)
+    if ((st = lincomb(ctx, qn_bar, RK_A3, g3, RK_A2, b2, 1.0, b1, s)) != MFC_OK) return st;
+    if ((st = lincomb(ctx, r, dt, b1, 0.0, nullptr, 0.0, nullptr, s)) != MFC_OK) return st;
+    return eval_L_vjp(ctx, q_n, r, qn_bar, s);
+}
+
+mfc_status mfc_check(mfc_ctx* ctx, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pending CUDA error");
+    return read_flag(ctx, (cudaStream_t)stream);
+}
+
+const char* mfc_last_error(const mfc_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Host-side launch table, one instance per number of fluids (each compiled
+// in its own translation unit so the builds run in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mfc_device.cuh"
+
+namespace mfc {
+
+// What the sweep does with its per-direction contribution t of cell c:
+//   acc_in = 0: Lc = t;  acc_in = 1: Lc = rhs[c] + t
+//   out_kind = 0: rhs[c] = Lc
+//   out_kind = 1: qout[c] = q[c] + dt Lc                       (RK3 stage 1)
+//   out_kind = 2: qout[c] = rk_a qn[c] + rk_b (q[c] + dt Lc)   (RK3 stages 2, 3)
+struct SweepArgs {
+    const double* q;      // stage input (stencil source)
+    double* rhs;          // accumulated right-hand side
+    const double* qn;     // q^n for out_kind 2 (may alias qout)
+    double* qout;         // stage output for out_kind 1, 2
+    const double* dt;     // device scalar
+    double rk_a, rk_b;
+    int acc_in, out_kind;
+    int seg;              // cells per thread along the sweep axis
+    int nseg;             // segments per line
+    int* flag;            // non-physical flag
+};
+
+// Adjoint sweep: qbar[c] += (contribution of axis `dir` to (dL/dq)^T rbar)[c].
+struct VjpArgs {
+    const double* q;      // state at which L is linearised
+    const double* rbar;   // adjoint of L (interior cells are read)
+    double* qbar;         // accumulated (interior cells)
+    int seg;              // cells per thread along the sweep axis
+    int nseg;             // segments per line
+};
+
+struct LaunchFns {
+    // One directional sweep of L(q) (precision 0 = FP64, 1 = mixed).
+    cudaError_t (*sweep)(const Consts& C, int dir, int precision, SweepArgs A, cudaStream_t s);
+    // CFL minimum of dx_d / (|u_d| + c) into *minbits (atomicMin).
+    cudaError_t (*cfl)(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s);
+    cudaError_t (*prim_to_cons)(const Consts& C, const double* w, double* q, cudaStream_t s);
+    cudaError_t (*cons_to_prim)(const Consts& C, const double* q, double* w, int* flag, cudaStream_t s);
+    // One directional sweep of the adjoint of L (see mfc_vjp.cuh).
+    cudaError_t (*sweep_vjp)(const Consts& C, int dir, int precision, VjpArgs A, cudaStream_t s);
+};
+
+const LaunchFns& launch_fns_nf1();
+const LaunchFns& launch_fns_nf2();
+const LaunchFns& launch_fns_nf3();
+const LaunchFns& launch_fns_nf4();
+
+// Cells per thread along a sweep of `n` cells with `nlines` lines.
+int sweep_segment(int64_t n, int64_t nlines);
+
+}  // namespace mfc

@@ -1,0 +1,209 @@
+// Adjoint sweep: one directional contribution of (dL/dq)^T rbar.
+#pragma once
+
+#include "mfc_adjoint.cuh"
+#include "mfc_device.cuh"
+#include "mfc_launch.h"
+
+namespace mfc {
+
+// One thread owns the cells [s0, s1) of one line along axis DIR and gathers
+// every contribution to them (no atomics): it recomputes the forward states
+// of the faces s0 - 5/2 .. s1 + 3/2 and runs, face by face, the adjoint of
+// the flux difference and alpha div(u) term, of HLLC and of WENO5; the
+// primitive-state bars of a cell are complete three faces after its own and
+// are then pulled back through conservative-to-primitive and added to
+// qbar.  Contributions to ghost cells are folded into the interior cell the
+// ghost copies (normal momentum negated across a reflective wall); for a
+// periodic axis the segments that own the copied cells collect those
+// contributions in a short pass over the far end of the line first.
+template <int NF, int ND, int DIR, class R>
+__global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
+    using L = Lay<NF, ND>;
+    constexpr int NQ = L::NQ;
+    constexpr int TA = (DIR == 0) ? 1 : 0;
+    constexpr int TB = (DIR == 2) ? 1 : 2;
+    const int64_t nta = C.n[TA], ntb = C.n[TB];
+    const int64_t nlines = nta * ntb;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nlines * A.nseg) return;
+    const int64_t line = tid % nlines;
+    const int64_t seg = tid / nlines;
+    const int64_t ia = line % nta, ib = line / nta;
+    const int64_t base = C.origin + ia * C.stride[TA] + ib * C.stride[TB];
+    const int64_t S = C.stride[DIR];
+    const int64_t fs = C.fstride;
+    const int64_t n = C.n[DIR];
+    const int64_t s0 = seg * A.seg;
+    const int64_t s1 = (s0 + A.seg < n) ? s0 + A.seg : n;
+    const int bclo = C.bc_lo[DIR], bchi = C.bc_hi[DIR];
+    const bool periodic = bclo == BC_PERIODIC;
+    const int variant = C.weno;
+    const R eps = sizeof(R) == 8 ? R(C.eps) : R(C.epsf);
+    const R inv_dx = R(C.inv_dx[DIR]);
+
+    R Wr[8][NQ];       // forward primitive states, ring indexed by cell & 7
+    R acc[8][NQ];      // primitive-state bars, same ring
+    R ufr[8];          // forward face velocities, ring indexed by face & 7
+    R ext_lo[3][NQ];   // periodic: bars of ghosts n..n+2, i.e. of cells 0..2
+    R ext_hi[3][NQ];   // periodic: bars of ghosts -3..-1, i.e. of cells n-3..n-1
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) ext_lo[a][k] = ext_hi[a][k] = R(0);
+
+    auto load_prim = [&](int64_t c, R* out) {
+        bool flip = false;
+        const int64_t cc = bc_source(c, n, bclo, bchi, flip);
+        const double* p = A.q + base + cc * S;
+        double qc[NQ], w[NQ];
+        bool bad = false;
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * fs);
+        if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
+        cons_to_prim<NF, ND>(qc, w, C, bad);
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) out[f] = R(w[f]);
+    };
+    auto rbar = [&](int64_t c, int k) -> R {
+        return (c >= 0 && c < n) ? R(__ldg(A.rbar + base + c * S + k * fs)) : R(0);
+    };
+
+    // pass 0: periodic, segments owning cells 0..2: contributions of the far
+    //         end to ghosts n..n+2 (copies of cells 0..2);
+    // pass 1: periodic, segments owning cells n-3..n-1: contributions of the
+    //         near end to ghosts -3..-1 (copies of cells n-3..n-1);
+    // pass 2: the faces and cells that touch the segment itself.
+    // Each pass runs j over [jb, je]: face j (= j+1/2) is processed for
+    // j <= fmax, the WENO adjoint of cell j for cmin <= j <= cmax, and cell
+    // j-3 is finished in pass 2.
+    for (int pass = 0; pass < 3; ++pass) {
+        int64_t jb, je, fmax, cmin, cmax;
+        if (pass == 0) {
+            if (!(periodic && s0 < 3)) continue;
+            jb = n - 3; je = n; fmax = n - 1; cmin = n - 2; cmax = n;
+        } else if (pass == 1) {
+            if (!(periodic && s1 > n - 3)) continue;
+            jb = -1; je = 1; fmax = 1; cmin = -1; cmax = 1;
+        } else {
+            jb = (s0 - 3 > -1) ? s0 - 3 : -1;
+            je = s1 + 2;
+            cmin = (jb == -1) ? -1 : jb + 1;
+            // a non-periodic segment owning one of cells n-3..n-1 also collects
+            // the mirrored / copied contributions of ghosts n..n+2
+            const bool ext = !periodic && s1 >= n - 2;
+            fmax = ext ? n - 1 : ((s1 + 1 < n - 1) ? s1 + 1 : n - 1);
+            cmax = ext ? n : ((s1 + 1 < n) ? s1 + 1 : n);
+        }
+        // contributions to cell x, routed according to the pass
+        auto sink = [&](int64_t x, int k, R v) {
+            if (pass == 0) {
+                if (x >= n && x < n + 3) ext_lo[x - n][k] += v;
+            } else if (pass == 1) {
+                if (x >= -3 && x < 0) ext_hi[x + 3][k] += v;
+            } else if (x >= 0 && x < n) {
+                acc[x & 7][k] += v;
+            } else if (!periodic) {
+                bool flip = false;
+                const int64_t img = bc_source(x, n, bclo, bchi, flip);
+                acc[img & 7][k] += (flip && k == L::MOM + DIR) ? -v : v;
+            }
+        };
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) acc[s][k] = R(0);
+        for (int64_t c = jb - 2; c <= jb + 2; ++c) load_prim(c, Wr[c & 7]);
+        // forward left state of face jb (right edge of cell jb)
+        R WLcur[NQ], WRbprev[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            R vl, vr;
+            weno5_cell<R>(Wr[(jb - 2) & 7][k], Wr[(jb - 1) & 7][k], Wr[jb & 7][k], Wr[(jb + 1) & 7][k],
+                          Wr[(jb + 2) & 7][k], variant, eps, vl, vr);
+            WLcur[k] = vr;
+            WRbprev[k] = R(0);
+        }
+        for (int64_t j = jb; j <= je; ++j) {
+            const bool face = (j >= -1) && (j <= fmax);
+            const bool cellw = (j >= cmin) && (j <= cmax);
+            if (face) load_prim(j + 3, Wr[(j + 3) & 7]);  // j + 3 <= n + 2
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) acc[(j + 3) & 7][k] = R(0);
+            R WLb[NQ], WRb[NQ], WLnext[NQ];
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) WLb[k] = WRb[k] = R(0);
+            if (face) {
+                // forward right state of face j (left edge of cell j+1), and left state of face j+1
+                R WRj[NQ];
+#pragma unroll
+                for (int k = 0; k < NQ; ++k)
+                    weno5_cell<R>(Wr[(j - 1) & 7][k], Wr[j & 7][k], Wr[(j + 1) & 7][k], Wr[(j + 2) & 7][k],
+                                  Wr[(j + 3) & 7][k], variant, eps, WRj[k], WLnext[k]);
+                // bars of the face flux and face velocity from rbar of cells j and j+1
+                R Fb[NQ];
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) Fb[k] = (rbar(j + 1, k) - rbar(j, k)) * inv_dx;
+                R ufb = R(0);
+#pragma unroll
+                for (int a = 0; a < NF - 1; ++a) {
+                    const int k = L::A + a;
+                    ufb += (rbar(j, k) * Wr[j & 7][k] - rbar(j + 1, k) * Wr[(j + 1) & 7][k]) * inv_dx;
+                }
+                R uf;
+                hllc_adj<NF, ND, DIR, R>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
+                ufr[j & 7] = uf;
+            } else {
+                ufr[j & 7] = R(0);
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) WLnext[k] = R(0);
+            }
+            if (cellw) {
+                // adjoint of the WENO5 reconstruction of cell j: right edge = face j (WLb),
+                // left edge = face j-1 (WRbprev)
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    R f[5], fb[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) f[m] = Wr[(j - 2 + m) & 7][k];
+                    weno5_cell_adj<R>(f, WRbprev[k], WLb[k], variant, eps, fb);
+#pragma unroll
+                    for (int m = 0; m < 5; ++m)
+                        if (fb[m] != R(0)) sink(j - 2 + m, k, fb[m]);
+                }
+            }
+            // finish cell j-3
+            const int64_t c = j - 3;
+            if (pass == 2 && c >= s0 && c < s1) {
+                const int64_t off = base + c * S;
+                double qc[NQ], wb[NQ], qb[NQ];
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    qc[k] = __ldg(A.q + off + k * fs);
+                    double v = double(acc[c & 7][k]);
+                    if (periodic && c < 3) v += double(ext_lo[c][k]);
+                    if (periodic && c >= n - 3) v += double(ext_hi[c - (n - 3)][k]);
+                    wb[k] = v;
+                    qb[k] = 0.0;
+                }
+                cons_to_prim_adj<NF, ND>(qc, wb, C, qb);
+                // alpha_c (u_{c+1/2} - u_{c-1/2}) / dx
+                const double du = double(ufr[c & 7]) - double(ufr[(c - 1) & 7]);
+#pragma unroll
+                for (int a = 0; a < NF - 1; ++a) {
+                    const int k = L::A + a;
+                    qb[k] += double(rbar(c, k)) * du * double(inv_dx);
+                }
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) A.qbar[off + k * fs] += qb[k];
+            }
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                WRbprev[k] = WRb[k];
+                WLcur[k] = WLnext[k];
+            }
+        }
+    }
+}
+
+}  // namespace mfc

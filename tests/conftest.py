@@ -18,3 +18,19 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def mfc_lib():
+    """The CUDA library, built in-tree (nvcc cross-compiles without a GPU)."""
+    from paper_2503_07953_gb300 import build, mfc
+    build.build()
+    return mfc
+
+
+@pytest.fixture(scope="session")
+def cuda_device():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    return torch.device("cuda", 0)

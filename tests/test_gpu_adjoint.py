@@ -1,0 +1,153 @@
+"""The hand-written adjoint (mfc_rhs_vjp, mfc_rk3_step_vjp) against the
+oracle's forward-mode derivatives of the same computation.
+
+Dot-product identity <v, J w> = <J^T v, w> with J w from the oracle's dual
+numbers and J^T v from the CUDA adjoint; full Jacobians on tiny grids
+(every column from the oracle, every row from the GPU); central finite
+differences of the GPU's own forward step.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_07953_gb300 import workloads as wl
+from tests.helpers import oracle_problem, solver_for, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def smooth_case(dims, bc_lo, bc_hi, gamma=(1.4, 4.4), pi=(0.0, 10.0), seed=3):
+    nd = len(dims)
+    hi = [1.0, 0.9, 0.8][:nd]
+    case = wl.Case("adj", list(dims), [0.0] * nd, hi, list(bc_lo), list(bc_hi), list(gamma), list(pi),
+                   cfl=0.4, steps=0)
+    return case, wl.random_smooth_state(case, seed=seed, amp=0.15)
+
+
+CASES = {
+    "smooth_3d_mixed_bc": lambda: smooth_case((11, 9, 7), (0, 1, 2), (0, 2, 1)),
+    "smooth_2d_periodic": lambda: smooth_case((19, 17), (0, 0), (0, 0)),
+    "shock_bubble_3d": lambda: wl.shock_bubble_3d(dims=(21, 18, 17)),
+    "water_air_1d": lambda: wl.water_air_shock_tube(300),
+    "random_interfaces_3d": lambda: wl.random_interfaces_3d(dims=(12, 11, 10)),
+}
+
+
+def dot(a, b):
+    return float(np.sum(a * b))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_vjp_dot_product(oracle_lib, mfc_lib, cuda_device, name):
+    case, W = CASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q = oracle_lib.prim_to_cons(P, W)
+    rng = np.random.default_rng(7)
+    scale = np.abs(q).max(axis=(1, 2, 3), keepdims=True)
+    w = rng.normal(size=q.shape) * scale
+    v = rng.normal(size=q.shape)
+    _, Jw = oracle_lib.rhs_jvp(P, q, w)
+    qb = S.rhs_vjp(S.from_interior(q), S.from_interior(v))
+    lhs = dot(v, Jw)
+    rhs = dot(to_host(S, qb), w)
+    assert rhs == pytest.approx(lhs, rel=1e-10), (lhs, rhs)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rk3_step_vjp_dot_product(oracle_lib, mfc_lib, cuda_device, name):
+    case, W = CASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q = oracle_lib.prim_to_cons(P, W)
+    dt = oracle_lib.cfl_dt(P, q, case.cfl)
+    rng = np.random.default_rng(8)
+    scale = np.abs(q).max(axis=(1, 2, 3), keepdims=True)
+    w = rng.normal(size=q.shape) * scale
+    v = rng.normal(size=q.shape) / scale
+    _, Jw = oracle_lib.rk3_step_jvp(P, q, w, dt)
+    qb = S.rk3_step_vjp(S.from_interior(q), dt, S.from_interior(v))
+    lhs = dot(v, Jw)
+    rhs = dot(to_host(S, qb), w)
+    assert rhs == pytest.approx(lhs, rel=1e-10), (lhs, rhs)
+
+
+@pytest.mark.parametrize("dims,bc_lo,bc_hi", [
+    ((17,), (2,), (2,)),        # two segments, the second one cell long, reflective
+    ((19,), (0,), (0,)),        # periodic with two segments
+    ((40,), (1,), (2,)),        # three segments, transmissive / reflective
+    ((6, 5), (0, 2), (0, 1)),   # 2D, every boundary type
+    ((3, 4), (0, 1), (0, 1)),   # smallest periodic axis
+])
+def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi):
+    """Every column of dL/dq from the oracle's dual numbers equals every row
+    of the GPU adjoint: the transposed Jacobian matches entry by entry."""
+    case, W = smooth_case(dims, bc_lo, bc_hi)
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q = oracle_lib.prim_to_cons(P, W)
+    N = q.size
+    J = np.empty((N, N))
+    for j in range(N):
+        e = np.zeros(N); e[j] = 1.0
+        J[:, j] = oracle_lib.rhs_jvp(P, q, e.reshape(q.shape))[1].ravel()
+    qg = S.from_interior(q)
+    JT = np.empty((N, N))
+    for i in range(N):
+        e = np.zeros(N); e[i] = 1.0
+        JT[i] = to_host(S, S.rhs_vjp(qg, S.from_interior(e.reshape(q.shape)))).ravel()
+    scale = np.abs(J).max()
+    assert np.abs(JT - J).max() <= 1e-12 * scale
+
+
+def test_rk3_step_vjp_central_differences(mfc_lib, cuda_device):
+    """The GPU adjoint against central differences of the GPU's own step."""
+    case, W = wl.shock_bubble_3d(dims=(20, 18, 16))
+    S = solver_for(mfc_lib, case)
+    q = S.prim_to_cons(S.from_interior(W))
+    dt = S.compute_dt(q)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    scale = torch.stack([S.interior(q)[k].abs().max() for k in range(S.nq)]).view(-1, 1, 1, 1)
+    w = S.from_interior(torch.randn(S.interior_shape, generator=gen, dtype=torch.float64).to(q.device) * scale)
+    v = S.from_interior(torch.randn(S.interior_shape, generator=gen, dtype=torch.float64).to(q.device) / scale)
+    qb = S.rk3_step_vjp(q, dt, v)
+    h = 1e-6
+    qp = q + h * w
+    qm = q - h * w
+    S.rk3_step(qp, dt)
+    S.rk3_step(qm, dt)
+    fd = float((S.interior(v) * (S.interior(qp) - S.interior(qm))).sum()) / (2 * h)
+    ad = float((S.interior(qb) * S.interior(w)).sum())
+    assert ad == pytest.approx(fd, rel=1e-6)
+
+
+def test_mixed_precision_adjoint_dot_product(oracle_lib, mfc_lib, cuda_device):
+    """Float32 reconstruction / Riemann adjoint: same identity at float32 accuracy."""
+    case, W = wl.shock_bubble_3d(dims=(21, 18, 17))
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_MIXED)
+    q = oracle_lib.prim_to_cons(P, W)
+    dt = oracle_lib.cfl_dt(P, q, case.cfl)
+    rng = np.random.default_rng(9)
+    scale = np.abs(q).max(axis=(1, 2, 3), keepdims=True)
+    w = rng.normal(size=q.shape) * scale
+    v = rng.normal(size=q.shape) / scale
+    _, Jw = oracle_lib.rk3_step_jvp(P, q, w, dt)
+    qb = S.rk3_step_vjp(S.from_interior(q), dt, S.from_interior(v))
+    assert dot(to_host(S, qb), w) == pytest.approx(dot(v, Jw), rel=1e-4)
+
+
+def test_vjp_aliasing_and_arguments(mfc_lib, cuda_device):
+    case, W = wl.shock_bubble_3d(dims=(12, 10, 9))
+    S = solver_for(mfc_lib, case)
+    q = S.prim_to_cons(S.from_interior(W))
+    dt = S.compute_dt(q)
+    g = S.from_interior(torch.ones(S.interior_shape, dtype=torch.float64))
+    ref = S.rk3_step_vjp(q, dt, g)
+    g2 = g.clone()
+    S.rk3_step_vjp(q, dt, g2, g2)  # qn_bar may alias qnp1_bar
+    assert torch.equal(S.interior(ref), S.interior(g2))
+    with pytest.raises(mfc_lib.MfcError):
+        S.rk3_step_vjp(q, 0.0, g)  # the adjoint needs the step's dt
+    with pytest.raises(mfc_lib.MfcError):
+        S.rhs_vjp(q, g, q)
