@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--workload", default="shock_bubble_3d",
                     choices=["shock_bubble_3d", "random_interfaces_3d", "bubble_collapse_2d", "water_air_1d"])
     ap.add_argument("--n", type=int, default=0, help="cells per axis (0: the workload's own size)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_fast", "mixed"])
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed, adjoint, e2e and CPU legs")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -183,12 +183,13 @@ def time_sweeps(S, q, reps: int) -> float:
     return e0.elapsed_time(e1) / (reps * S.ndim)
 
 
-def field_errors(a: torch.Tensor, b: torch.Tensor):
-    out = []
-    for k in range(b.shape[0]):
-        den = b[k].abs().max().item()
-        out.append((a[k] - b[k]).abs().max().item() / den if den > 0 else 0.0)
-    return out
+def field_errors(a: torch.Tensor, b: torch.Tensor, nf: int, nd: int):
+    """Per field max |a - b| / max |b|; the momentum components share the
+    largest of their maxima as scale."""
+    den = [b[k].abs().max().item() for k in range(b.shape[0])]
+    m = max(den[nf:nf + nd])
+    den[nf:nf + nd] = [m] * nd
+    return [(a[k] - b[k]).abs().max().item() / den[k] if den[k] > 0 else 0.0 for k in range(b.shape[0])]
 
 
 def cpu_baseline_leg(workload: str, sample_n: int, steps: int) -> dict:
@@ -262,12 +263,31 @@ def make_workload_stub(args):
     return c
 
 
+PREC = {"fp64": 0, "mixed": 1, "fp64_fast": 2}
+
+
+def time_vjp(S, q, dt: float, reps: int) -> float:
+    """Milliseconds per mfc_rk3_step_vjp (stage recomputation included)."""
+    g = S.empty()
+    g.copy_(q)
+    out = S.empty()
+    stream = torch.cuda.current_stream()
+    S.rk3_step_vjp(q, dt, g, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        S.rk3_step_vjp(q, dt, g, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def run_ours(args, world, rank, local):
     from paper_2503_07953_gb300 import build, mfc
     build.build()
-    dev = torch.device("cuda", torch.cuda.current_device())
     case, W = make_workload(args.workload, args.n)
-    prec = mfc.MFC_MIXED if args.precision == "mixed" else mfc.MFC_FP64
+    prec = PREC[args.precision]
     S = mfc.Solver.from_case(case, precision=prec)
     q0 = S.prim_to_cons(S.from_interior(W))
     del W
@@ -289,21 +309,22 @@ def run_ours(args, world, rank, local):
     value = world * ncell * args.steps / (ms / 1e3)
 
     # dominant kernel: the directional sweep (per launch, CUDA events)
-    t_sweep = time_sweeps(S, q, 5)
+    t_sweep = time_sweeps(S, q, 3)
     per_sweep = flops.per_cell_sweep(args.workload) * ncell
     achieved = per_sweep / (t_sweep / 1e3) / 1e12
-    peak = FP64_PEAK_TFLOPS if prec == mfc.MFC_FP64 else None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if peak else None, "traffic": None,
-            "kernel": f"sweep_kernel ({'FP64' if prec == mfc.MFC_FP64 else 'mixed'}), "
-                      f"{t_sweep:.3f} ms per launch, {per_sweep / 1e9:.2f} GFLOP per launch",
-            "peak_basis": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)"}
-    if prec == mfc.MFC_MIXED:
-        roof["peak_basis"] = "mixed path: FP32 and FP64 pipes both in use, see DESIGN.md"
+    fp64 = prec != mfc.MFC_MIXED
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS if fp64 else None, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if fp64 else None, "traffic": None,
+            "kernel": f"sweep_kernel ({args.precision}), {t_sweep:.3f} ms per launch, "
+                      f"{per_sweep / 1e9:.2f} GFLOP (algorithmic) per launch",
+            "peak_basis": "FP64 pipe: 152 SMs x 2 DFMA lanes/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s "
+                          "(unit counts and max clock; 1.253 measured by a DFMA microbenchmark)"}
+    if not fp64:
+        roof["peak_basis"] = "mixed path: FP32 and FP64 pipes both in use"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == mfc.MFC_FP64 else "f64+f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f64+f32",
             "data": "synthetic",
             "config": {"workload": describe(case), "cells": ncell, "precision": args.precision,
                        "dt": "CFL dt reduced on the device every step",
@@ -314,25 +335,39 @@ def run_ours(args, world, rank, local):
 
     if not args.no_extras and rank == 0:
         extras = {}
-        # mixed precision on the same workload, and its error against FP64
-        if prec == mfc.MFC_FP64:
-            Sm = mfc.Solver.from_case(case, precision=mfc.MFC_MIXED)
-            qm = q0.clone()
+        # reference trajectory for the error of the other precisions
+        qref = q0.clone()
+        S.rk3_run(qref, args.warmup + args.steps, 0.0)
+        for name in ("fp64", "fp64_fast", "mixed"):
+            if name == args.precision:
+                continue
+            So = mfc.Solver.from_case(case, precision=PREC[name])
+            qo = q0.clone()
             for _ in range(args.warmup):
-                Sm.rk3_step(qm, 0.0)
-            msm = time_steps(Sm, qm, args.steps)
-            Sm.check()
-            # error after warmup + steps steps from the same initial state
-            qf = q0.clone()
-            S.rk3_run(qf, args.warmup + args.steps, 0.0)
-            errs = field_errors(Sm.interior(qm), S.interior(qf))
-            t_sw_m = time_sweeps(Sm, qm, 5)
-            extras["mixed"] = {"value": ncell * args.steps / (msm / 1e3), "ms_per_step": msm / args.steps,
-                               "speedup_vs_fp64": ms / msm,
-                               "field_max_rel_err_vs_fp64": errs,
-                               "after_steps": args.warmup + args.steps,
-                               "sweep_ms_per_launch": t_sw_m}
-            del Sm, qm, qf
+                So.rk3_step(qo, 0.0)
+            mso = time_steps(So, qo, args.steps)
+            So.check()
+            extras[name] = {"value": ncell * args.steps / (mso / 1e3), "ms_per_step": mso / args.steps,
+                            "speedup_vs_" + args.precision: ms / mso,
+                            "field_max_rel_err_vs_" + args.precision: field_errors(So.interior(qo), S.interior(qref),
+                                                                                  case.nf, case.ndim),
+                            "after_steps": args.warmup + args.steps,
+                            "sweep_ms_per_launch": time_sweeps(So, qo, 3)}
+            if name == "mixed":
+                extras[name]["bitwise_equal_to_" + args.precision] = None
+            else:
+                extras[name]["bitwise_equal_to_" + args.precision] = bool(torch.equal(So.interior(qo),
+                                                                                      S.interior(qref)))
+            del So, qo
+            torch.cuda.empty_cache()
+        del qref
+        # adjoint cost: one RK3-step VJP (stages recomputed) per forward step
+        dt = S.compute_dt(q)
+        ms_fwd1 = time_steps(S, q.clone(), 2) / 2
+        ms_vjp = time_vjp(S, q, dt, 2)
+        extras["vjp"] = {"ms_per_step_vjp": ms_vjp, "ms_per_step_fwd": ms_fwd1, "vjp_over_fwd": ms_vjp / ms_fwd1,
+                         "precision": args.precision}
+        torch.cuda.empty_cache()
         # end to end through the public API with host buffers
         host_in = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
         host_out = torch.empty(q.shape, dtype=torch.float64, pin_memory=True)
@@ -357,7 +392,8 @@ def run_ours(args, world, rank, local):
         line.update(extras)
         sample_n = 64 if case.ndim == 3 else 0
         line["cpu_baseline"] = cpu_baseline_leg(args.workload, sample_n, 5 if case.ndim == 3 else 50)
-    print(json.dumps(line), flush=True) if rank == 0 else None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():

@@ -66,11 +66,18 @@ typedef enum {
 
 typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2 } mfc_bc;
 
-/* MFC_FP64: everything in float64.
+/* MFC_FP64: everything in float64, every operation in the order of the
+ *   defining formula with IEEE division and square root and no fused
+ *   multiply-add, so results are reproducible bit for bit (and equal to a
+ *   plain CPU evaluation of the same formulas).
+ * MFC_FP64_FAST: float64 with the WENO weight divisions folded into one
+ *   reciprocal per normalisation and fused multiply-adds; agrees with
+ *   MFC_FP64 to rounding.
  * MFC_MIXED: WENO5 reconstruction, HLLC and the per-direction flux
- * difference in float32; conservative-to-primitive conversion, the sum over
- * directions, the Runge-Kutta stage update and the CFL reduction in float64. */
-typedef enum { MFC_FP64 = 0, MFC_MIXED = 1 } mfc_precision;
+ *   difference in float32; conservative-to-primitive conversion, the sum
+ *   over directions, the Runge-Kutta stage update and the CFL reduction in
+ *   float64. */
+typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2 } mfc_precision;
 
 /* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2). */
 typedef enum { MFC_WENO_JS = 0, MFC_WENO_M = 1, MFC_WENO_Z = 2 } mfc_weno;

@@ -246,10 +246,10 @@ def block_counts(P: Problem, qa, qb) -> dict:
     """Operation counts of one call of each building block (see the C source)."""
     lib = _load(); c = P.cstruct()
     qa = np.ascontiguousarray(qa, dtype=np.float64); qb = np.ascontiguousarray(qb, dtype=np.float64)
-    out = np.zeros((7, 5), dtype=np.int64)
+    out = np.zeros((8, 5), dtype=np.int64)
     _check(lib.oc_block_counts(ctypes.byref(c), _dp(qa), _dp(qb),
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "block_counts")
-    names = ("c2p", "weno_edge", "hllc", "cell_term", "rk_update", "cfl_cell", "weno_beta")
+    names = ("c2p", "weno_edge", "hllc", "cell_term", "rk_update", "cfl_cell", "weno_beta", "face_check")
     keys = ("add", "mul", "div", "sqrt", "cmp")
     return {n: dict(zip(keys, out[i].tolist())) for i, n in enumerate(names)}
 

@@ -231,6 +231,16 @@ template <class T> T sound_speed(T rho, T p, T Gamma, T Pi) {
     return sqrt(c2);
 }
 
+/* A primitive state is a physical mixture when rho > 0, Gamma > 0 and
+ * (Gamma + 1) p + Pi > 0 (so that c^2 > 0). */
+template <class T> bool physical_state(const Lay& L, const Eos& eos, const T* w) {
+    T rho = w[L.rho(0)];
+    for (int i = 1; i < L.nf; ++i) rho = rho + w[L.rho(i)];
+    T Gamma, Pi;
+    eos.mix(w + L.alpha(0), Gamma, Pi);
+    return val(rho) > 0.0 && val(Gamma) > 0.0 && val((Gamma + T(1.0)) * w[L.E()] + Pi) > 0.0;
+}
+
 /* ------------------------------------------------------------------ */
 /* WENO5 (Sec. 3.2.1, Sec. 4.2.2)                                      */
 /* ------------------------------------------------------------------ */
@@ -462,6 +472,15 @@ void face_flux(const View& V, const Lay& L, const Eos& eos, int ax, const int* c
         WL[k] = weno5_edge(f, true, P.weno, P.eps);
         for (int m = 0; m < 5; ++m) f[m] = W[m + 1][k];
         WR[k] = weno5_edge(f, false, P.weno, P.eps);
+    }
+    /* Positivity reading (the paper is silent): if either reconstructed
+     * state is not a physical mixture, the face falls back to first-order
+     * reconstruction, i.e. the states of its two cells. */
+    if (!physical_state(L, eos, WL) || !physical_state(L, eos, WR)) {
+        for (int k = 0; k < L.nq(); ++k) {
+            WL[k] = W[2][k];
+            WR[k] = W[3][k];
+        }
     }
     hllc(L, eos, ax, WL, WR, F, uf);
 }
@@ -815,7 +834,8 @@ int oc_rk3_step_count(const oc_problem* P, const double* q, double dt, int64_t* 
  * term of one direction, row 4 one RK3 stage update of one cell (the costlier
  * stage form a*qn + b*(q + dt*L)), row 5 the CFL quantity of one cell,
  * row 6 the smoothness indicators of one five-cell stencil (shared by the
- * two edge values of a cell).  out: 7 rows x 5 counts. */
+ * two edge values of a cell), row 7 the physical-state test of both
+ * reconstructed states of one face.  out: 8 rows x 5 counts. */
 int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int64_t* out) {
     if (check_problem(P)) return -1;
     Lay L{P->nf, P->ndim};
@@ -858,6 +878,9 @@ int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int
     Cnt bt[3];
     weno5_beta(f, bt);
     take(6);
+    physical_state(L, eos, wa);
+    physical_state(L, eos, wb);
+    take(7);
     return 0;
 }
 

@@ -21,7 +21,10 @@ LIB = os.path.join(BUILD, "libmfcgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["mfc_api.cu", "mfc_nf1.cu", "mfc_nf2.cu", "mfc_nf3.cu", "mfc_nf4.cu"]
+SOURCES = ["mfc_api.cu"] + [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast")]
+# The exact-arithmetic kernels follow the defining formulas operation by
+# operation: no FMA contraction there.
+PER_SOURCE_FLAGS = {src: ["--fmad=false"] for src in SOURCES if src.endswith("_exact.cu")}
 
 
 def nvcc() -> str:
@@ -41,6 +44,7 @@ def _fingerprint() -> str:
                 with open(p, "rb") as fh:
                     h.update(fh.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(repr(sorted(PER_SOURCE_FLAGS.items())).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -58,7 +62,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *PER_SOURCE_FLAGS.get(src, []), *extra_flags, "-c",
+               os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -142,10 +142,11 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
     const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
     const R A1 = f[1] - R(2) * f[2] + f[3], B1 = f[1] - f[3];
     const R A2 = f[2] - R(2) * f[3] + f[4], B2 = R(3) * f[2] - R(4) * f[3] + f[4];
-    R beta[3];
-    beta[0] = c13 * (A0 * A0) + c14 * (B0 * B0);
-    beta[1] = c13 * (A1 * A1) + c14 * (B1 * B1);
-    beta[2] = c13 * (A2 * A2) + c14 * (B2 * B2);
+    // indicators as the forward weights use them (scaled by `scale` in
+    // float32); the weights depend only on ratios of eps + beta, so the bar
+    // of the unscaled beta is the bar of the scaled one times the scale
+    R beta[3], e, scale;
+    weno5_scaled_beta(f[0], f[1], f[2], f[3], f[4], eps, beta, e, scale);
     R betab[3] = {R(0), R(0), R(0)};
     const R sixth = R(1) / R(6);
     if (vrb != R(0)) {
@@ -154,7 +155,7 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
         p[0] = (R(2) * f[0] - R(7) * f[1] + R(11) * f[2]) / R(6);
         p[1] = (-f[1] + R(5) * f[2] + R(2) * f[3]) / R(6);
         p[2] = (R(2) * f[2] + R(5) * f[3] - f[4]) / R(6);
-        weno5_edge_adj(p, beta, d, variant, eps, vrb, pb, betab);
+        weno5_edge_adj(p, beta, d, variant, e, vrb, pb, betab);
         fb[0] += (R(2) * pb[0]) * sixth;
         fb[1] += (R(-7) * pb[0] - pb[1]) * sixth;
         fb[2] += (R(11) * pb[0] + R(5) * pb[1] + R(2) * pb[2]) * sixth;
@@ -167,13 +168,16 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
         p[0] = (-f[0] + R(5) * f[1] + R(2) * f[2]) / R(6);
         p[1] = (R(2) * f[1] + R(5) * f[2] - f[3]) / R(6);
         p[2] = (R(11) * f[2] - R(7) * f[3] + R(2) * f[4]) / R(6);
-        weno5_edge_adj(p, beta, d, variant, eps, vlb, pb, betab);
+        weno5_edge_adj(p, beta, d, variant, e, vlb, pb, betab);
         fb[0] += (-pb[0]) * sixth;
         fb[1] += (R(5) * pb[0] + R(2) * pb[1]) * sixth;
         fb[2] += (R(2) * pb[0] + R(5) * pb[1] + R(11) * pb[2]) * sixth;
         fb[3] += (-pb[1] - R(7) * pb[2]) * sixth;
         fb[4] += (R(2) * pb[2]) * sixth;
     }
+    betab[0] *= scale;
+    betab[1] *= scale;
+    betab[2] *= scale;
     // beta_r = c13 A_r^2 + c14 B_r^2
     const R a0 = R(2) * c13 * A0 * betab[0], b0 = R(2) * c14 * B0 * betab[0];
     const R a1 = R(2) * c13 * A1 * betab[1], b1 = R(2) * c14 * B1 * betab[1];

@@ -30,7 +30,9 @@ struct mfc_ctx {
     mfc_eos eos;
     mfc_opts opts;
     mfc::Consts C;
-    const mfc::LaunchFns* fns;
+    const mfc::LaunchFns* exact;  // CFL, maps and the MFC_FP64 sweeps
+    const mfc::LaunchFns* fns;    // the sweeps of the chosen precision
+    int mode;                     // mfc::MODE_* of the sweeps
     int device;
     int64_t total;        // doubles in a state-sized buffer
     double* q1 = nullptr;  // RK stage 1
@@ -141,7 +143,8 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
         if (!(e->gamma[i] > 1.0) || !std::isfinite(e->gamma[i])) return "gamma must be > 1";
         if (!(e->pi_inf[i] >= 0.0) || !std::isfinite(e->pi_inf[i])) return "pi_inf must be >= 0";
     }
-    if (o->precision != MFC_FP64 && o->precision != MFC_MIXED) return "unknown precision";
+    if (o->precision != MFC_FP64 && o->precision != MFC_MIXED && o->precision != MFC_FP64_FAST)
+        return "unknown precision";
     if (o->weno < 0 || o->weno > 2) return "unknown WENO variant";
     if (!(o->weno_eps > 0.0) || !std::isfinite(o->weno_eps)) return "weno_eps must be > 0";
     if (!(o->cfl > 0.0) || !std::isfinite(o->cfl)) return "cfl must be > 0";
@@ -177,18 +180,27 @@ void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Co
         C.hf[i] = (float)C.h[i];
     }
     C.eps = o->weno_eps;
-    // float32 WENO: (eps + beta)^2 must stay a normal float when beta = 0
-    C.epsf = (float)(o->weno_eps < 1e-18 ? 1e-18 : o->weno_eps);
+    // float32 WENO rescales eps with the indicators and floors it (mfc_device.cuh)
+    C.epsf = (float)o->weno_eps;
     C.cfl = o->cfl;
     total = C.fstride * C.nq;
 }
 
-const mfc::LaunchFns* fns_for(int nf) {
+const mfc::LaunchFns* exact_fns_for(int nf) {
     switch (nf) {
-        case 1: return &mfc::launch_fns_nf1();
-        case 2: return &mfc::launch_fns_nf2();
-        case 3: return &mfc::launch_fns_nf3();
-        default: return &mfc::launch_fns_nf4();
+        case 1: return &mfc::launch_fns_exact_nf1();
+        case 2: return &mfc::launch_fns_exact_nf2();
+        case 3: return &mfc::launch_fns_exact_nf3();
+        default: return &mfc::launch_fns_exact_nf4();
+    }
+}
+
+const mfc::LaunchFns* fast_fns_for(int nf) {
+    switch (nf) {
+        case 1: return &mfc::launch_fns_fast_nf1();
+        case 2: return &mfc::launch_fns_fast_nf2();
+        case 3: return &mfc::launch_fns_fast_nf3();
+        default: return &mfc::launch_fns_fast_nf4();
     }
 }
 
@@ -198,7 +210,7 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
     set_scalars_kernel<<<1, 1, 0, s>>>(ctx->scal, dt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "set scalars");
     if (dt > 0.0) return MFC_OK;
-    if ((e = ctx->fns->cfl(ctx->C, q, &ctx->scal->minbits, &ctx->scal->flag, s)) != cudaSuccess)
+    if ((e = ctx->exact->cfl(ctx->C, q, &ctx->scal->minbits, &ctx->scal->flag, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "cfl kernel");
     finalize_dt_kernel<<<1, 1, 0, s>>>(ctx->scal, ctx->C.cfl, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "finalize dt");
@@ -223,7 +235,7 @@ mfc_status eval_L(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, co
         A.rk_a = a;
         A.rk_b = b;
         A.flag = &ctx->scal->flag;
-        cudaError_t e = ctx->fns->sweep(ctx->C, d, ctx->opts.precision, A, s);
+        cudaError_t e = ctx->fns->sweep(ctx->C, d, ctx->mode, A, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep kernel");
     }
     return MFC_OK;
@@ -264,7 +276,7 @@ mfc_status eval_L_vjp(mfc_ctx* ctx, const double* q, const double* rbar, double*
         A.q = q;
         A.rbar = rbar;
         A.qbar = qbar;
-        cudaError_t e = ctx->fns->sweep_vjp(ctx->C, d, ctx->opts.precision, A, s);
+        cudaError_t e = ctx->fns->sweep_vjp(ctx->C, d, ctx->mode, A, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint sweep kernel");
     }
     return MFC_OK;
@@ -328,7 +340,14 @@ mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* op
     ctx->eos = *eos;
     ctx->opts = *opts;
     make_consts(grid, eos, opts, ctx->C, ctx->total);
-    ctx->fns = fns_for(eos->nfluids);
+    ctx->exact = exact_fns_for(eos->nfluids);
+    if (opts->precision == MFC_FP64) {
+        ctx->fns = ctx->exact;
+        ctx->mode = mfc::MODE_EXACT;
+    } else {
+        ctx->fns = fast_fns_for(eos->nfluids);
+        ctx->mode = opts->precision == MFC_MIXED ? mfc::MODE_MIXED : mfc::MODE_FAST;
+    }
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
         g_init_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
@@ -373,7 +392,7 @@ mfc_status mfc_prim_to_cons(mfc_ctx* ctx, const double* w, double* q, void* stre
     MFC_CHECK_CTX(ctx);
     if (!w || !q) return fail(ctx, MFC_ERR_ARG, "null buffer");
     DeviceGuard guard(ctx->device);
-    cudaError_t e = ctx->fns->prim_to_cons(ctx->C, w, q, (cudaStream_t)stream);
+    cudaError_t e = ctx->exact->prim_to_cons(ctx->C, w, q, (cudaStream_t)stream);
     return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "prim_to_cons");
 }
 
@@ -381,7 +400,7 @@ mfc_status mfc_cons_to_prim(mfc_ctx* ctx, const double* q, double* w, void* stre
     MFC_CHECK_CTX(ctx);
     if (!w || !q) return fail(ctx, MFC_ERR_ARG, "null buffer");
     DeviceGuard guard(ctx->device);
-    cudaError_t e = ctx->fns->cons_to_prim(ctx->C, q, w, &ctx->scal->flag, (cudaStream_t)stream);
+    cudaError_t e = ctx->exact->cons_to_prim(ctx->C, q, w, &ctx->scal->flag, (cudaStream_t)stream);
     return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "cons_to_prim");
 }
 

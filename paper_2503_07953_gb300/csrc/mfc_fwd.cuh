@@ -15,9 +15,14 @@ namespace mfc {
 // known.  Boundary cells are read through bc_source (no ghost layer is
 // read).  Consecutive threads take consecutive lines; for DIR = 1, 2 those
 // are consecutive x, so every load is coalesced.
-template <int NF, int ND, int DIR, class R>
+//
+// Positivity reading (the paper is silent): when either reconstructed
+// state of a face is not a physical mixture, the face uses the states of
+// its two cells (first-order reconstruction) instead.
+template <int NF, int ND, int DIR, int MODE>
 __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepArgs A) {
     using L = Lay<NF, ND>;
+    using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
     constexpr int TA = (DIR == 0) ? 1 : 0;
     constexpr int TB = (DIR == 2) ? 1 : 2;
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
 #pragma unroll
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * C.fstride);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
-        cons_to_prim<NF, ND>(qc, w, C, bad);
+        cons_to_prim<NF, ND, MODE>(qc, w, C, bad);
 #pragma unroll
         for (int f = 0; f < NQ; ++f) out[f] = R(w[f]);
     };
@@ -65,8 +70,16 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
         R WRm[NQ], WLm[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k)
-            weno5_cell<R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, WRm[k], WLm[k]);
+            weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, WRm[k], WLm[k]);
         if (m >= s0) {
+            // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)
+            if (!physical_state<NF, ND, R>(WLprev, C) || !physical_state<NF, ND, R>(WRm, C)) {
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    WLprev[k] = W[1][k];
+                    WRm[k] = W[2][k];
+                }
+            }
             R F[NQ], uf;
             hllc<NF, ND, DIR, R>(WLprev, WRm, C, F, uf, bad);
             if (m >= s0 + 1) {
@@ -76,7 +89,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     R t;
-                    if constexpr (sizeof(R) == 8) {
+                    if constexpr (MODE == MODE_EXACT) {
                         t = (Fprev[k] - F[k]) / dx;
                         if (k >= L::A) t = t + W[1][k] * du / dx;
                     } else {

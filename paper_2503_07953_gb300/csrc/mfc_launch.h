@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mfc_device.cuh"
 
 namespace mfc {
@@ -36,20 +38,28 @@ struct VjpArgs {
 };
 
 struct LaunchFns {
-    // One directional sweep of L(q) (precision 0 = FP64, 1 = mixed).
-    cudaError_t (*sweep)(const Consts& C, int dir, int precision, SweepArgs A, cudaStream_t s);
-    // CFL minimum of dx_d / (|u_d| + c) into *minbits (atomicMin).
+    // One directional sweep of L(q); mode is MODE_EXACT for the exact
+    // tables and MODE_FAST or MODE_MIXED for the others.
+    cudaError_t (*sweep)(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+    // One directional sweep of the adjoint of L (see mfc_vjp.cuh).
+    cudaError_t (*sweep_vjp)(const Consts& C, int dir, int mode, VjpArgs A, cudaStream_t s);
+    // Exact tables only: CFL minimum of dx_d / (|u_d| + c) into *minbits
+    // (atomicMin), and the primitive / conservative maps.
     cudaError_t (*cfl)(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s);
     cudaError_t (*prim_to_cons)(const Consts& C, const double* w, double* q, cudaStream_t s);
     cudaError_t (*cons_to_prim)(const Consts& C, const double* q, double* w, int* flag, cudaStream_t s);
-    // One directional sweep of the adjoint of L (see mfc_vjp.cuh).
-    cudaError_t (*sweep_vjp)(const Consts& C, int dir, int precision, VjpArgs A, cudaStream_t s);
 };
 
-const LaunchFns& launch_fns_nf1();
-const LaunchFns& launch_fns_nf2();
-const LaunchFns& launch_fns_nf3();
-const LaunchFns& launch_fns_nf4();
+// Exact tables (MODE_EXACT, built without FMA contraction) and fast tables
+// (MODE_FAST, MODE_MIXED) for N_f = 1 .. 4.
+const LaunchFns& launch_fns_exact_nf1();
+const LaunchFns& launch_fns_exact_nf2();
+const LaunchFns& launch_fns_exact_nf3();
+const LaunchFns& launch_fns_exact_nf4();
+const LaunchFns& launch_fns_fast_nf1();
+const LaunchFns& launch_fns_fast_nf2();
+const LaunchFns& launch_fns_fast_nf3();
+const LaunchFns& launch_fns_fast_nf4();
 
 // Cells per thread along a sweep of `n` cells with `nlines` lines.
 int sweep_segment(int64_t n, int64_t nlines);

@@ -1,5 +1,7 @@
-// Launch wrappers, instantiated once per number of fluids NF by
-// mfc_nf<NF>.cu.  ND (1..3), the sweep direction and the precision are
+// Launch wrappers.  Each translation unit mfc_nf<NF>_<exact|fast>.cu
+// instantiates them for one number of fluids NF and one family of
+// arithmetic modes (MODE_EXACT, compiled without FMA contraction; or
+// MODE_FAST and MODE_MIXED).  ND (1..3) and the sweep direction are
 // dispatched here to the kernel templates.
 #pragma once
 
@@ -24,76 +26,81 @@ inline unsigned stride_grid(int64_t n, int block) {
     return (unsigned)b;
 }
 
-template <int NF, int ND>
-cudaError_t sweep_nd(const Consts& C, int dir, int precision, SweepArgs A, cudaStream_t s) {
+template <int NF, int ND, int DIR, int MODE>
+void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream_t s) {
+    sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
+}
+
+template <int NF, int ND, int DIR, int MODE>
+void launch_sweep_vjp(unsigned grid, const Consts& C, const VjpArgs& A, cudaStream_t s) {
+    sweep_vjp_kernel<NF, ND, DIR, MODE><<<grid, kSweepVjpBlock, 0, s>>>(C, A);
+}
+
+// MODE_EXACT when EXACT, else MODE_FAST / MODE_MIXED as asked.
+template <int NF, int ND, bool EXACT>
+cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s) {
     const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];
     A.seg = sweep_segment(C.n[dir], nlines);
     A.nseg = (int)((C.n[dir] + A.seg - 1) / A.seg);
     const int64_t threads = nlines * A.nseg;
+    if (threads == 0) return cudaSuccess;
     const unsigned grid = grid_for(threads, kSweepBlock);
-    if (threads == 0) return cudaSuccess;
-#define MFC_SWEEP(D)                                                                              \
-    do {                                                                                          \
-        if (precision == 0)                                                                       \
-            sweep_kernel<NF, ND, D, double><<<grid, kSweepBlock, 0, s>>>(C, A);                   \
-        else                                                                                      \
-            sweep_kernel<NF, ND, D, float><<<grid, kSweepBlock, 0, s>>>(C, A);                    \
-    } while (0)
-    if (dir == 0) {
-        MFC_SWEEP(0);
-    } else if constexpr (ND >= 2) {
-        if (dir == 1) {
-            MFC_SWEEP(1);
-        } else if constexpr (ND >= 3) {
-            MFC_SWEEP(2);
+    auto go = [&](auto dirc) {
+        constexpr int D = decltype(dirc)::value;
+        if constexpr (EXACT) {
+            launch_sweep<NF, ND, D, MODE_EXACT>(grid, C, A, s);
+        } else {
+            if (mode == MODE_MIXED)
+                launch_sweep<NF, ND, D, MODE_MIXED>(grid, C, A, s);
+            else
+                launch_sweep<NF, ND, D, MODE_FAST>(grid, C, A, s);
         }
-    }
-#undef MFC_SWEEP
+    };
+    if (dir == 0) go(std::integral_constant<int, 0>());
+    if constexpr (ND >= 2) if (dir == 1) go(std::integral_constant<int, 1>());
+    if constexpr (ND >= 3) if (dir == 2) go(std::integral_constant<int, 2>());
     return cudaGetLastError();
 }
 
-template <int NF, int ND>
-cudaError_t sweep_vjp_nd(const Consts& C, int dir, int precision, VjpArgs A, cudaStream_t s) {
+template <int NF, int ND, bool EXACT>
+cudaError_t sweep_vjp_nd(const Consts& C, int dir, int mode, VjpArgs A, cudaStream_t s) {
     const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];
     A.seg = sweep_segment(C.n[dir], nlines);
     A.nseg = (int)((C.n[dir] + A.seg - 1) / A.seg);
     const int64_t threads = nlines * A.nseg;
-    const unsigned grid = grid_for(threads, kSweepVjpBlock);
     if (threads == 0) return cudaSuccess;
-#define MFC_SWEEP_VJP(D)                                                                          \
-    do {                                                                                          \
-        if (precision == 0)                                                                       \
-            sweep_vjp_kernel<NF, ND, D, double><<<grid, kSweepVjpBlock, 0, s>>>(C, A);            \
-        else                                                                                      \
-            sweep_vjp_kernel<NF, ND, D, float><<<grid, kSweepVjpBlock, 0, s>>>(C, A);             \
-    } while (0)
-    if (dir == 0) {
-        MFC_SWEEP_VJP(0);
-    } else if constexpr (ND >= 2) {
-        if (dir == 1) {
-            MFC_SWEEP_VJP(1);
-        } else if constexpr (ND >= 3) {
-            MFC_SWEEP_VJP(2);
+    const unsigned grid = grid_for(threads, kSweepVjpBlock);
+    auto go = [&](auto dirc) {
+        constexpr int D = decltype(dirc)::value;
+        if constexpr (EXACT) {
+            launch_sweep_vjp<NF, ND, D, MODE_EXACT>(grid, C, A, s);
+        } else {
+            if (mode == MODE_MIXED)
+                launch_sweep_vjp<NF, ND, D, MODE_MIXED>(grid, C, A, s);
+            else
+                launch_sweep_vjp<NF, ND, D, MODE_FAST>(grid, C, A, s);
         }
-    }
-#undef MFC_SWEEP_VJP
+    };
+    if (dir == 0) go(std::integral_constant<int, 0>());
+    if constexpr (ND >= 2) if (dir == 1) go(std::integral_constant<int, 1>());
+    if constexpr (ND >= 3) if (dir == 2) go(std::integral_constant<int, 2>());
     return cudaGetLastError();
 }
 
-template <int NF>
+template <int NF, bool EXACT>
 struct Launch {
-    static cudaError_t sweep(const Consts& C, int dir, int precision, SweepArgs A, cudaStream_t s) {
+    static cudaError_t sweep(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s) {
         switch (C.nd) {
-            case 1: return sweep_nd<NF, 1>(C, dir, precision, A, s);
-            case 2: return sweep_nd<NF, 2>(C, dir, precision, A, s);
-            default: return sweep_nd<NF, 3>(C, dir, precision, A, s);
+            case 1: return sweep_nd<NF, 1, EXACT>(C, dir, mode, A, s);
+            case 2: return sweep_nd<NF, 2, EXACT>(C, dir, mode, A, s);
+            default: return sweep_nd<NF, 3, EXACT>(C, dir, mode, A, s);
         }
     }
-    static cudaError_t sweep_vjp(const Consts& C, int dir, int precision, VjpArgs A, cudaStream_t s) {
+    static cudaError_t sweep_vjp(const Consts& C, int dir, int mode, VjpArgs A, cudaStream_t s) {
         switch (C.nd) {
-            case 1: return sweep_vjp_nd<NF, 1>(C, dir, precision, A, s);
-            case 2: return sweep_vjp_nd<NF, 2>(C, dir, precision, A, s);
-            default: return sweep_vjp_nd<NF, 3>(C, dir, precision, A, s);
+            case 1: return sweep_vjp_nd<NF, 1, EXACT>(C, dir, mode, A, s);
+            case 2: return sweep_vjp_nd<NF, 2, EXACT>(C, dir, mode, A, s);
+            default: return sweep_vjp_nd<NF, 3, EXACT>(C, dir, mode, A, s);
         }
     }
     static cudaError_t cfl(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s) {
@@ -127,7 +134,8 @@ struct Launch {
         return cudaGetLastError();
     }
     static const LaunchFns& fns() {
-        static const LaunchFns f = {&sweep, &cfl, &p2c, &c2p, &sweep_vjp};
+        static const LaunchFns f = {&sweep, &sweep_vjp, EXACT ? &cfl : nullptr, EXACT ? &p2c : nullptr,
+                                    EXACT ? &c2p : nullptr};
         return f;
     }
 };

@@ -17,9 +17,10 @@ namespace mfc {
 // ghost copies (normal momentum negated across a reflective wall); for a
 // periodic axis the segments that own the copied cells collect those
 // contributions in a short pass over the far end of the line first.
-template <int NF, int ND, int DIR, class R>
+template <int NF, int ND, int DIR, int MODE>
 __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
     using L = Lay<NF, ND>;
+    using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
     constexpr int TA = (DIR == 0) ? 1 : 0;
     constexpr int TB = (DIR == 2) ? 1 : 2;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
 #pragma unroll
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * fs);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
-        cons_to_prim<NF, ND>(qc, w, C, bad);
+        cons_to_prim<NF, ND, MODE>(qc, w, C, bad);
 #pragma unroll
         for (int f = 0; f < NQ; ++f) out[f] = R(w[f]);
     };
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             R vl, vr;
-            weno5_cell<R>(Wr[(jb - 2) & 7][k], Wr[(jb - 1) & 7][k], Wr[jb & 7][k], Wr[(jb + 1) & 7][k],
-                          Wr[(jb + 2) & 7][k], variant, eps, vl, vr);
+            weno5_cell<MODE, R>(Wr[(jb - 2) & 7][k], Wr[(jb - 1) & 7][k], Wr[jb & 7][k], Wr[(jb + 1) & 7][k],
+                                Wr[(jb + 2) & 7][k], variant, eps, vl, vr);
             WLcur[k] = vr;
             WRbprev[k] = R(0);
         }
@@ -138,8 +139,18 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 R WRj[NQ];
 #pragma unroll
                 for (int k = 0; k < NQ; ++k)
-                    weno5_cell<R>(Wr[(j - 1) & 7][k], Wr[j & 7][k], Wr[(j + 1) & 7][k], Wr[(j + 2) & 7][k],
-                                  Wr[(j + 3) & 7][k], variant, eps, WRj[k], WLnext[k]);
+                    weno5_cell<MODE, R>(Wr[(j - 1) & 7][k], Wr[j & 7][k], Wr[(j + 1) & 7][k], Wr[(j + 2) & 7][k],
+                                        Wr[(j + 3) & 7][k], variant, eps, WRj[k], WLnext[k]);
+                // first-order fallback of the forward pass at a non-physical face
+                const bool first_order =
+                    !physical_state<NF, ND, R>(WLcur, C) || !physical_state<NF, ND, R>(WRj, C);
+                if (first_order) {
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) {
+                        WLcur[k] = Wr[j & 7][k];
+                        WRj[k] = Wr[(j + 1) & 7][k];
+                    }
+                }
                 // bars of the face flux and face velocity from rbar of cells j and j+1
                 R Fb[NQ];
 #pragma unroll
@@ -153,6 +164,15 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 R uf;
                 hllc_adj<NF, ND, DIR, R>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
                 ufr[j & 7] = uf;
+                if (first_order) {
+                    // the face states are the cell states themselves
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) {
+                        if (WLb[k] != R(0)) sink(j, k, WLb[k]);
+                        if (WRb[k] != R(0)) sink(j + 1, k, WRb[k]);
+                        WLb[k] = WRb[k] = R(0);
+                    }
+                }
             } else {
                 ufr[j & 7] = R(0);
 #pragma unroll

@@ -217,17 +217,59 @@ def _fourier_curl(seed: int, X, Y, Z, modes: int = 32, kmax: int = 4):
     return ux, uy, uz
 
 
+def random_interfaces_window(origin=(200, 180, 160), dims=(32, 32, 32), n: int = 512, steps: int = 50) -> tuple:
+    """A dims-sized block, at cell offset `origin`, of the n^3 random
+    interface field below: the same fields at the same resolution (the
+    pressure noise is a function of the global cell index), with
+    transmissive boundaries in place of the periodic wrap."""
+    h = 1.0 / n
+    lo = [origin[a] * h for a in range(3)]
+    hi = [(origin[a] + dims[a]) * h for a in range(3)]
+    case = Case("random_interfaces_window", list(dims), lo, hi, [TRANSMISSIVE] * 3, [TRANSMISSIVE] * 3,
+                [1.4, 4.4, 6.1], [0.0, 6.0e8, 2.0e9], cfl=0.4, steps=steps)
+    return case, _random_interfaces_fields(case, origin, n)
+
+
 def random_interfaces_3d(n: int = 512, steps: int = 50, dims=None) -> tuple:
     """3D three-fluid random interface field on the periodic unit cube:
     fluids (gamma, pi_inf) = (1.4, 0), (4.4, 6e8), (6.1, 2e9) with phasic
     densities 1.2, 1000, 1100; alpha = softmax of three 32-mode Fourier
     fields (amplitude 4, seeds 0, 1, 2) clipped to [1e-6, 1] and renormalised;
-    p = 1e5 (1 + 0.01 U[-1,1)) (seed 4); u = curl of a random vector
-    potential (seed 3) scaled to max |u| = 10 m/s; CFL 0.4."""
+    p = 1e5 (1 + 0.01 U[-1,1)) with U a hash of the global cell index
+    (seed 4); u = curl of a random vector potential (seed 3) scaled so that
+    its maximum over a 64^3 sampling of the cube is 10 m/s; CFL 0.4."""
     nx, ny, nz = dims if dims is not None else (n, n, n)
     case = Case("random_interfaces_3d", [nx, ny, nz], [0.0] * 3, [1.0] * 3,
                 [PERIODIC] * 3, [PERIODIC] * 3, [1.4, 4.4, 6.1], [0.0, 6.0e8, 2.0e9],
                 cfl=0.4, steps=steps)
+    return case, _random_interfaces_fields(case, (0, 0, 0), nx)
+
+
+def _hash_uniform(seed: int, gi, gj, gk, n: int) -> np.ndarray:
+    """U[-1, 1) from the splitmix64 finaliser of the global cell index."""
+    with np.errstate(over="ignore"):
+        x = (gi.astype(np.uint64) + np.uint64(n) * (gj.astype(np.uint64) + np.uint64(n) * gk.astype(np.uint64))
+             + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15))
+        x = x + np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    return (x >> np.uint64(11)).astype(np.float64) * (2.0 / 2.0 ** 53) - 1.0
+
+
+_CURL_SCALE = {}
+
+
+def _curl_scale() -> float:
+    """10 m/s over the maximum speed of the raw curl field on a 64^3 sampling."""
+    if "s" not in _CURL_SCALE:
+        c = (np.arange(64) + 0.5) / 64
+        ux, uy, uz = _fourier_curl(3, c[None, None, :], c[None, :, None], c[:, None, None])
+        _CURL_SCALE["s"] = 10.0 / np.sqrt(ux ** 2 + uy ** 2 + uz ** 2).max()
+    return _CURL_SCALE["s"]
+
+
+def _random_interfaces_fields(case: Case, origin, n: int) -> np.ndarray:
     X, Y, Z = _centres(case)
     phi = np.stack([_fourier_field(s, X, Y, Z, amp=4.0) for s in (0, 1, 2)])
     phi = phi - phi.max(axis=0, keepdims=True)
@@ -236,13 +278,16 @@ def random_interfaces_3d(n: int = 512, steps: int = 50, dims=None) -> tuple:
     alpha = np.clip(alpha, 1e-6, 1.0)
     alpha = alpha / alpha.sum(axis=0, keepdims=True)
     shp = case.shape[1:]
-    p = 1.0e5 * (1.0 + 0.01 * _uniform(4, shp))
+    nx, ny, nz = case.n
+    gi = (origin[0] + np.arange(nx))[None, None, :]
+    gj = (origin[1] + np.arange(ny))[None, :, None]
+    gk = (origin[2] + np.arange(nz))[:, None, None]
+    gi, gj, gk = np.broadcast_arrays(gi, gj, gk)
+    p = 1.0e5 * (1.0 + 0.01 * _hash_uniform(4, gi, gj, gk, n))
     ux, uy, uz = _fourier_curl(3, X, Y, Z)
-    umax = np.sqrt(ux ** 2 + uy ** 2 + uz ** 2).max()
-    scale = 10.0 / umax
+    scale = _curl_scale()
     rhos = [np.full(shp, 1.2), np.full(shp, 1000.0), np.full(shp, 1100.0)]
-    W = _assemble(case, [alpha[0], alpha[1], alpha[2]], rhos, [ux * scale, uy * scale, uz * scale], p)
-    return case, W
+    return _assemble(case, [alpha[0], alpha[1], alpha[2]], rhos, [ux * scale, uy * scale, uz * scale], p)
 
 
 def bubble_collapse_2d(n: int = 1024, steps: int = 500, dims=None) -> tuple:

@@ -41,7 +41,8 @@ def test_per_step_total_is_close_to_the_oracle_count(oracle_lib):
     ncell = 6 ** 3
     faces = 36 * 7  # the oracle computes the n + 1 faces of each of the 36 lines
     # oracle: per face 6 c2p and 2 nq full edges; per cell one cell term per direction
-    oracle_per_sweep = faces * (6 * b["c2p"] + 2 * b["nq"] * b["weno_edge"] + b["hllc"]) + ncell * b["cell_term"]
+    oracle_per_sweep = faces * (6 * b["c2p"] + 2 * b["nq"] * b["weno_edge"] + b["face_check"] + b["hllc"]) \
+        + ncell * b["cell_term"]
     rk = ncell * (3 * b["rk_update"] - 2 * b["nq"])  # stage 1 is q + dt L: 2 ops per field instead of 5
     # accumulation into L: nq adds per cell per direction
     acc = ncell * b["nq"] * 3

@@ -1,23 +1,29 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerance: per field, max |gpu - oracle| / max |oracle| <= 1e-11 (the FP64
-target), for one evaluation of L, one step, or 100+ steps.  The two sides
-round differently only where the GPU contracts a*b + c into one FMA; one
-evaluation already differs by up to ~1e-12 where the flux difference
-cancels (energy next to pi_inf ~ 1e9, or a momentum field whose maximum is
-small).
+MFC_FP64 evaluates every formula in the oracle's operation order with IEEE
+division and square root and no fused multiply-add, so it must agree with
+the oracle bit for bit, for one evaluation of L and after 100+ steps.
+
+MFC_FP64_FAST differs from the oracle by rounding only; per field,
+max |gpu - oracle| / max |oracle| <= 1e-11 (the FP64 target) on workloads
+whose own rounding sensitivity is far below that (the 3D shock-bubble).
+Momentum components share one scale (tests.helpers.field_errors).
+
+Some workloads amplify rounding by many orders of magnitude (measured on
+the oracle itself: a 1-ulp perturbation of the 1D water/air state grows to
+~1e-6 in 200 steps with WENO-M's eps = 1e-40), which is why the
+reproducible mode exists and carries the long-run comparisons.
 """
 import numpy as np
 import pytest
 import torch
 
 from paper_2503_07953_gb300 import workloads as wl
-from tests.helpers import field_errors, oracle_problem, solver_for, to_host
+from tests.helpers import case_errors, oracle_problem, solver_for, to_host
 
 pytestmark = pytest.mark.gpu
 
-TOL_ONE = 1e-11
-TOL_RUN = 1e-11
+TOL = 1e-11
 
 
 def four_fluid_case(dims=(13, 11, 9)):
@@ -32,7 +38,7 @@ def sod_single_fluid(n=200):
 
 CASES = {
     "shock_bubble_3d": lambda: wl.shock_bubble_3d(dims=(37, 29, 21)),
-    "random_interfaces_3d": lambda: wl.random_interfaces_3d(dims=(18, 17, 15)),
+    "random_interfaces_3d": lambda: wl.random_interfaces_window(dims=(26, 24, 22)),
     "bubble_collapse_2d": lambda: wl.bubble_collapse_2d(dims=(41, 33)),
     "water_air_1d": lambda: wl.water_air_shock_tube(1000),
     "sod_single_fluid_1d": lambda: sod_single_fluid(),
@@ -50,80 +56,103 @@ def setup(oracle_lib, mfc_lib, make, **kw):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_prim_cons_maps(oracle_lib, mfc_lib, cuda_device, name):
+def test_prim_cons_maps_bitwise(oracle_lib, mfc_lib, cuda_device, name):
     case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, CASES[name])
-    assert (field_errors(to_host(S, q_g), q_o) <= 1e-15).all()
-    w_g = to_host(S, S.cons_to_prim(q_g))
-    w_o = oracle_lib.cons_to_prim(P, q_o)
-    assert (field_errors(w_g, w_o) <= 1e-13).all()
+    assert np.array_equal(to_host(S, q_g), q_o)
+    assert np.array_equal(to_host(S, S.cons_to_prim(q_g)), oracle_lib.cons_to_prim(P, q_o))
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_rhs_matches_oracle(oracle_lib, mfc_lib, cuda_device, name):
+def test_rhs_bitwise(oracle_lib, mfc_lib, cuda_device, name):
     case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, CASES[name])
     L_o, bad = oracle_lib.rhs(P, q_o, return_bad=True)
     assert bad == 0
     L_g = to_host(S, S.rhs(S.from_interior(q_o)))
-    err = field_errors(L_g, L_o)
-    assert (err <= TOL_ONE).all(), err
+    assert np.array_equal(L_g, L_o), case_errors(case, L_g, L_o)
     S.check()
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_fast_and_mixed(oracle_lib, mfc_lib, cuda_device, name):
+    """MFC_FP64_FAST to rounding; MFC_MIXED to float32 accuracy."""
+    case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, CASES[name], precision=mfc_lib.MFC_FP64_FAST)
+    L_o = oracle_lib.rhs(P, q_o)
+    err = case_errors(case, to_host(S, S.rhs(S.from_interior(q_o))), L_o)
+    assert (err <= TOL).all(), err
+    Sm = solver_for(mfc_lib, case, precision=mfc_lib.MFC_MIXED)
+    err = case_errors(case, to_host(Sm, Sm.rhs(Sm.from_interior(q_o))), L_o)
+    assert (err <= 1e-4).all(), err
+
+
 @pytest.mark.parametrize("weno", [0, 2])
-def test_rhs_weno_variants(oracle_lib, mfc_lib, cuda_device, weno):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_rhs_weno_variants(oracle_lib, mfc_lib, cuda_device, weno, prec):
     case, W = wl.shock_bubble_3d(dims=(19, 16, 14))
     case.weno = weno
     case.eps = 1e-6 if weno == 0 else 1e-40
     P = oracle_problem(oracle_lib, case)
-    S = solver_for(mfc_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
     q_o = oracle_lib.prim_to_cons(P, W)
-    err = field_errors(to_host(S, S.rhs(S.from_interior(q_o))), oracle_lib.rhs(P, q_o))
-    assert (err <= TOL_ONE).all(), err
+    L_g = to_host(S, S.rhs(S.from_interior(q_o)))
+    L_o = oracle_lib.rhs(P, q_o)
+    if prec == mfc_lib.MFC_FP64:
+        assert np.array_equal(L_g, L_o)
+    else:
+        assert (case_errors(case, L_g, L_o) <= TOL).all()
 
 
-def test_compute_dt_matches_oracle(oracle_lib, mfc_lib, cuda_device):
+def test_compute_dt_bitwise(oracle_lib, mfc_lib, cuda_device):
     for make in (CASES["shock_bubble_3d"], CASES["water_air_1d"], CASES["random_interfaces_3d"]):
         case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, make)
-        dt_g = S.compute_dt(S.from_interior(q_o))
-        dt_o = oracle_lib.cfl_dt(P, q_o, case.cfl)
-        assert dt_g == pytest.approx(dt_o, rel=1e-14)
+        assert S.compute_dt(S.from_interior(q_o)) == oracle_lib.cfl_dt(P, q_o, case.cfl)
 
 
-@pytest.mark.parametrize("name,steps,dims", [
-    ("shock_bubble_3d", 100, (20, 18, 16)),
-    ("bubble_collapse_2d", 100, (40, 36)),
-    ("water_air_1d", 200, None),
-    ("random_interfaces_3d", 100, (12, 11, 10)),
-])
-def test_rk3_run_matches_oracle(oracle_lib, mfc_lib, cuda_device, name, steps, dims):
-    """100+ CFL-limited RK3 steps on both sides; the dt sequences and the
-    final states agree to <= 1e-11 per field (the FP64 target)."""
-    makers = {
-        "shock_bubble_3d": lambda: wl.shock_bubble_3d(dims=dims),
-        "bubble_collapse_2d": lambda: wl.bubble_collapse_2d(dims=dims),
-        "water_air_1d": lambda: wl.water_air_shock_tube(1000),
-        "random_interfaces_3d": lambda: wl.random_interfaces_3d(dims=dims),
-    }
-    case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, makers[name])
+RUNS = {
+    "shock_bubble_3d": (lambda: wl.shock_bubble_3d(dims=(20, 18, 16)), 100),
+    "bubble_collapse_2d": (lambda: wl.bubble_collapse_2d(dims=(64, 60)), 100),
+    "water_air_1d": (lambda: wl.water_air_shock_tube(1000), 200),
+    "random_interfaces_3d": (lambda: wl.random_interfaces_window(origin=(10, 300, 420), dims=(24, 22, 20)), 50),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RUNS))
+def test_rk3_run_bitwise(oracle_lib, mfc_lib, cuda_device, name):
+    """The paper-shaped workloads (small grids) for their full step counts
+    with the CFL dt of every step: identical dt sequences and final states."""
+    make, steps = RUNS[name]
+    case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, make)
     q_g = S.from_interior(q_o)
     dt_log = torch.zeros(steps, dtype=torch.float64, device=cuda_device)
     S.rk3_run(q_g, steps, 0.0, dt_log)
     S.check()
     q_end, dts, bad = oracle_lib.rk3_run(P, q_o, steps, cfl=case.cfl, return_bad=True)
     assert bad == 0
-    np.testing.assert_allclose(dt_log.cpu().numpy(), dts, rtol=1e-12)
-    err = field_errors(to_host(S, q_g), q_end)
-    assert (err <= TOL_RUN).all(), err
+    assert np.array_equal(dt_log.cpu().numpy(), dts)
+    got = to_host(S, q_g)
+    assert np.array_equal(got, q_end), case_errors(case, got, q_end)
 
 
-def test_full_size_step_sampled(oracle_lib, mfc_lib, cuda_device):
+def test_rk3_run_fast_shock_bubble(oracle_lib, mfc_lib, cuda_device):
+    """MFC_FP64_FAST, 100 CFL steps of the 3D shock-bubble: <= 1e-11 per field."""
+    make, steps = RUNS["shock_bubble_3d"]
+    case, W, P, S, q_o, q_g = setup(oracle_lib, mfc_lib, make, precision=mfc_lib.MFC_FP64_FAST)
+    q_g = S.from_interior(q_o)
+    S.rk3_run(q_g, steps, 0.0)
+    S.check()
+    q_end, dts = oracle_lib.rk3_run(P, q_o, steps, cfl=case.cfl)
+    err = case_errors(case, to_host(S, q_g), q_end)
+    assert (err <= TOL).all(), err
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_full_size_step_sampled(oracle_lib, mfc_lib, cuda_device, prec):
     """The 256^3 shock-bubble workload in the benchmarked configuration: one
     step on the GPU, checked at sampled cells (corners, walls, the shock and
     the bubble interface) against the oracle's domain-of-dependence
     evaluation of the same step."""
     case, W = wl.shock_bubble_3d(256)
     P = oracle_problem(oracle_lib, case)
-    S = solver_for(mfc_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
     q_g = S.prim_to_cons(S.from_interior(W))
     q_o = to_host(S, q_g)  # the oracle steps the GPU's own initial state
     dt = oracle_lib.cfl_dt(P, q_o, case.cfl)
@@ -136,9 +165,13 @@ def test_full_size_step_sampled(oracle_lib, mfc_lib, cuda_device):
     cells += [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(9)]
     ref = oracle_lib.rk3_step_sampled(P, q_o, dt, cells)
     got = np.stack([out_g[:, k, j, i] for (i, j, k) in cells])
-    scale = np.abs(out_g).max(axis=(1, 2, 3))
-    err = (np.abs(got - ref) / scale).max(axis=0)
-    assert (err <= TOL_ONE).all(), err
+    if prec == mfc_lib.MFC_FP64:
+        assert np.array_equal(got, ref)
+    else:
+        scale = np.abs(out_g).max(axis=(1, 2, 3))
+        scale[case.nf:case.nf + case.ndim] = scale[case.nf:case.nf + case.ndim].max()
+        err = (np.abs(got - ref) / scale).max(axis=0)
+        assert (err <= TOL).all(), err
 
 
 @pytest.mark.parametrize("ghost", [0, 5])
@@ -159,6 +192,7 @@ def test_ghost_padding_does_not_change_results(oracle_lib, mfc_lib, cuda_device,
     ((3, 3, 3), 0),
     ((7, 1), 1),          # one cell across a transmissive axis
     ((1, 6, 4), 1),
+    ((67, 3, 18), 2),     # ragged segments along x, smallest reflective axis
 ])
 def test_degenerate_sizes(oracle_lib, mfc_lib, cuda_device, dims, bc):
     nd = len(dims)
@@ -171,7 +205,21 @@ def test_degenerate_sizes(oracle_lib, mfc_lib, cuda_device, dims, bc):
     q_g = S.from_interior(q_o)
     S.rk3_run(q_g, 5)
     q_end, _ = oracle_lib.rk3_run(P, q_o, 5, cfl=case.cfl)
-    assert (field_errors(to_host(S, q_g), q_end) <= TOL_ONE).all()
+    assert np.array_equal(to_host(S, q_g), q_end)
+
+
+def test_positivity_fallback_matches_oracle(oracle_lib, mfc_lib, cuda_device):
+    """Three stiff fluids at 1e5 Pa on a coarse 24x22x20 grid of the whole
+    cube: WENO overshoots make thousands of reconstructed states
+    non-physical (c^2 < 0 without the fallback); both sides fall back to
+    first order at exactly those faces."""
+    case, W = wl.random_interfaces_3d(dims=(24, 22, 20))
+    P = oracle_problem(oracle_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    L_o, bad = oracle_lib.rhs(P, q_o, return_bad=True)
+    assert bad == 0
+    S = solver_for(mfc_lib, case)
+    assert np.array_equal(to_host(S, S.rhs(S.from_interior(q_o))), L_o)
 
 
 def test_nonphysical_state_reported(oracle_lib, mfc_lib, cuda_device):
