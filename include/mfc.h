@@ -163,6 +163,34 @@ mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, dou
 mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const double* qnp1_bar,
                             double* qn_bar, void* stream);
 
+/* Allocation-free variant of mfc_rk3_step, for callers that cannot
+ * allocate device memory: code that runs while another component owns the
+ * device's memory budget, code that must not take the device-wide
+ * synchronisation cudaMalloc and cudaFree imply, or a caller that keeps a
+ * fixed footprint.  (The paper has no counterpart: it is a property of
+ * this library, not of the method.)
+ *
+ * Same arguments and results as creating a context with grid / eos / opts
+ * and calling mfc_rk3_step, without the context: the step's scratch (two
+ * stage states, the right-hand side and the dt / flag scalars) is a
+ * file-scope device array of MFC_NOALLOC_SCRATCH_DOUBLES doubles (64 MiB)
+ * that every GPU loading the library holds until the process exits.  The
+ * state may hold at most (MFC_NOALLOC_SCRATCH_DOUBLES - 32) / 3 doubles
+ * (padded cells x fields); larger grids return MFC_ERR_ARG.  q and dt_used
+ * are DEVICE pointers, as for mfc_rk3_step.
+ *
+ * No cudaMalloc, cudaFree or other allocating routine is called.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents: calls that overlap on the GPU (concurrent
+ * streams, several host threads) race and must be serialised by the
+ * caller.  Non-physical states are not reported by this call (no context
+ * holds the flag).  Errors: mfc_last_error(NULL). */
+#define MFC_NOALLOC_SCRATCH_DOUBLES 8388608
+mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts, double* q,
+                                double dt, double* dt_used, void* stream);
+
 /* Synchronise the stream; report (and clear) the non-physical-state flag. */
 mfc_status mfc_check(mfc_ctx* ctx, void* stream);
 

@@ -495,3 +495,81 @@ const char* mfc_last_error(const mfc_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free RK3 step.  Its scratch (the two stage states, the
+// right-hand-side accumulator and the dt / flag scalars) is a file-scope
+// device array, so the call needs no context and allocates no device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocScalarDoubles = 32;  // 256 bytes in front of the state buffers
+static __device__ __align__(256) double g_noalloc_scratch[MFC_NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int kNoallocMaxDevices = 64;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts,
+                                           double* q, double dt, double* dt_used, void* stream) {
+    const std::string why = check_description(grid, eos, opts);
+    if (!why.empty()) {
+        g_init_error = why;
+        return MFC_ERR_ARG;
+    }
+    if (!q || !std::isfinite(dt)) {
+        g_init_error = "null state or non-finite dt";
+        return MFC_ERR_ARG;
+    }
+    mfc_ctx ctx;
+    make_consts(grid, eos, opts, ctx.C, ctx.total);
+    if (kNoallocScalarDoubles + 3 * ctx.total > (int64_t)MFC_NOALLOC_SCRATCH_DOUBLES) {
+        g_init_error = "state too large for the allocation-free step: 3 x (padded cells x fields) + 32 must not "
+                       "exceed MFC_NOALLOC_SCRATCH_DOUBLES";
+        return MFC_ERR_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        g_init_error = "no usable current CUDA device";
+        return MFC_ERR_CUDA;
+    }
+    // once per device, with that device current: the device address of the array
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            g_init_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return MFC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    double* base = g_noalloc_ptr[dev];
+    ctx.grid = *grid;
+    ctx.eos = *eos;
+    ctx.opts = *opts;
+    ctx.device = dev;
+    ctx.exact = exact_fns_for(eos->nfluids);
+    if (opts->precision == MFC_FP64) {
+        ctx.fns = ctx.exact;
+        ctx.mode = mfc::MODE_EXACT;
+    } else {
+        ctx.fns = fast_fns_for(eos->nfluids);
+        ctx.mode = opts->precision == MFC_MIXED ? mfc::MODE_MIXED : mfc::MODE_FAST;
+    }
+    ctx.scal = reinterpret_cast<DevScalars*>(base);
+    ctx.q1 = base + kNoallocScalarDoubles;
+    ctx.q2 = ctx.q1 + ctx.total;
+    ctx.r = ctx.q2 + ctx.total;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the non-physical flag is the only scratch value read before it is written
+    e = cudaMemsetAsync(&ctx.scal->flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("clearing the flag: ") + cudaGetErrorString(e);
+        return MFC_ERR_CUDA;
+    }
+    const mfc_status st = rk3_once(&ctx, q, dt, dt_used, s);
+    if (st != MFC_OK) g_init_error = ctx.err;
+    return st;
+}

@@ -73,6 +73,8 @@ _SIGS = {
     "mfc_rk3_step_vjp": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _VP, _VP]),
     "mfc_check": (ctypes.c_int, [_VP, _VP]),
     "mfc_last_error": (ctypes.c_char_p, [_VP]),
+    "mfc_rk3_step_noalloc": (ctypes.c_int, [ctypes.POINTER(mfc_grid), ctypes.POINTER(mfc_eos),
+                                            ctypes.POINTER(mfc_opts), _VP, ctypes.c_double, _VP, _VP]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -156,6 +158,12 @@ def mfc_rk3_step_vjp(ctx, q_n, dt, qnp1_bar, qn_bar, stream) -> None:
 
 def mfc_check(ctx, stream) -> None:
     _err(ctx, lib().mfc_check(ctx, stream))
+
+
+def mfc_rk3_step_noalloc(grid: mfc_grid, eos: mfc_eos, opts: mfc_opts, q, dt, dt_used, stream) -> None:
+    """One RK3 step without a context or any device allocation (see mfc.h)."""
+    _err(None, lib().mfc_rk3_step_noalloc(ctypes.byref(grid), ctypes.byref(eos), ctypes.byref(opts), q,
+                                          float(dt), dt_used, stream))
 
 
 def mfc_last_error(ctx) -> str:
