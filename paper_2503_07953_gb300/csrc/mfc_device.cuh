@@ -125,6 +125,54 @@ __device__ __forceinline__ void cons_to_prim(const double* q, double* w, const C
     w[L::E] = (q[L::E] - ke - Pi) / Gamma;
 }
 
+// Primitive state of one cell in the precision of the reconstruction.
+// MODE_EXACT / MODE_FAST: cons_to_prim in float64.  MODE_MIXED: the
+// cancelling part of the pressure recovery, rho E - Pi - |rho u|^2/(2 rho),
+// is evaluated in float64 (Pi from the float64 volume fractions, the
+// subtractions in float64); the kinetic energy, the velocities and the final
+// division by Gamma, whose relative errors carry into p unamplified, in
+// float32, as are the outputs.
+template <int NF, int ND, int MODE, class R>
+__device__ __forceinline__ void prim_for_recon(const double* q, R* out, const Consts& C, bool& bad) {
+    using L = Lay<NF, ND>;
+    if constexpr (MODE == MODE_MIXED) {
+        float rho = float(q[0]);
+#pragma unroll
+        for (int i = 1; i < NF; ++i) rho += float(q[i]);
+        bad |= !(rho > 0.0f);
+        const float irho = __fdividef(1.0f, rho);
+#pragma unroll
+        for (int i = 0; i < NF; ++i) out[i] = float(q[i]);
+        float ke = 0.0f;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const float m = float(q[L::MOM + d]);
+            out[L::MOM + d] = m * irho;
+            ke += m * out[L::MOM + d];
+        }
+        ke *= 0.5f;
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) s = s + q[L::A + j];
+        double Pi = (1.0 - s) * C.h[NF - 1];
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) Pi = Pi + q[L::A + j] * C.h[j];
+        const double num = (q[L::E] - Pi) - double(ke);
+        float Gamma = float(1.0 - s) * C.gf[NF - 1];
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) {
+            out[L::A + j] = float(q[L::A + j]);
+            Gamma += out[L::A + j] * C.gf[j];
+        }
+        out[L::E] = __fdividef(float(num), Gamma);
+    } else {
+        double w[Lay<NF, ND>::NQ];
+        cons_to_prim<NF, ND, MODE>(q, w, C, bad);
+#pragma unroll
+        for (int f = 0; f < Lay<NF, ND>::NQ; ++f) out[f] = R(w[f]);
+    }
+}
+
 // A primitive state is a physical mixture when rho > 0, Gamma > 0 and
 // (Gamma + 1) p + Pi > 0 (so that c^2 > 0).
 template <int NF, int ND, class R>

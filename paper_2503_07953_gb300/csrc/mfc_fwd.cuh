@@ -50,13 +50,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
         bool flip = false;
         const int64_t cc = bc_source(c, n, bclo, bchi, flip);
         const double* p = A.q + base + cc * S;
-        double qc[NQ], w[NQ];
+        double qc[NQ];
 #pragma unroll
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * C.fstride);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
-        cons_to_prim<NF, ND, MODE>(qc, w, C, bad);
-#pragma unroll
-        for (int f = 0; f < NQ; ++f) out[f] = R(w[f]);
+        prim_for_recon<NF, ND, MODE, R>(qc, out, C, bad);
     };
 
 #pragma unroll

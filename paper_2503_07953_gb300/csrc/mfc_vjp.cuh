@@ -57,14 +57,12 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
         bool flip = false;
         const int64_t cc = bc_source(c, n, bclo, bchi, flip);
         const double* p = A.q + base + cc * S;
-        double qc[NQ], w[NQ];
+        double qc[NQ];
         bool bad = false;
 #pragma unroll
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * fs);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
-        cons_to_prim<NF, ND, MODE>(qc, w, C, bad);
-#pragma unroll
-        for (int f = 0; f < NQ; ++f) out[f] = R(w[f]);
+        prim_for_recon<NF, ND, MODE, R>(qc, out, C, bad);
     };
     auto rbar = [&](int64_t c, int k) -> R {
         return (c >= 0 && c < n) ? R(__ldg(A.rbar + base + c * S + k * fs)) : R(0);

@@ -30,6 +30,20 @@ def field_errors(a, b, nf=None, nd=None):
     return np.array(out)
 
 
+def field_scales(case, q):
+    """Characteristic magnitude of each conserved field: the maximum for the
+    partial densities and the energy, sqrt(max rho * max rho E) (~ rho c)
+    for the momenta, 1 for the volume fractions."""
+    q = np.asarray(q)
+    nf, nd = case.nf, case.ndim
+    rho = np.sum(q[:nf], axis=0)
+    sc = np.array([max(np.abs(q[k]).max(), 1e-300) for k in range(q.shape[0])])
+    mom = np.sqrt(np.abs(rho).max() * np.abs(q[nf + nd]).max())
+    sc[nf:nf + nd] = mom
+    sc[nf + nd + 1:] = 1.0
+    return sc
+
+
 def case_errors(case, a, b):
     return field_errors(a, b, case.nf, case.ndim)
 

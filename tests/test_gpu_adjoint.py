@@ -25,7 +25,7 @@ import pytest
 import torch
 
 from paper_2503_07953_gb300 import workloads as wl
-from tests.helpers import oracle_problem, solver_for, to_host
+from tests.helpers import field_scales, oracle_problem, solver_for, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -62,10 +62,11 @@ def dot(a, b):
     return float(np.sum(a * b))
 
 
-def directions(q, seed):
+def directions(case, q, seed):
+    """w in the units of each field, v in the inverse units: <v, J w> is then a
+    sum of nondimensional terms."""
     rng = np.random.default_rng(seed)
-    scale = np.abs(q).max(axis=(1, 2, 3), keepdims=True)
-    scale = np.where(scale > 0, scale, 1.0)
+    scale = field_scales(case, q).reshape(-1, 1, 1, 1)
     return rng.normal(size=q.shape) * scale, rng.normal(size=q.shape) / scale
 
 
@@ -75,7 +76,7 @@ def test_rhs_vjp_dot_product(oracle_lib, mfc_lib, cuda_device, name, prec):
     P = oracle_problem(oracle_lib, case)
     S = solver_for(mfc_lib, case, precision=prec)
     q = oracle_lib.prim_to_cons(P, W)
-    w, v = directions(q, 7)
+    w, v = directions(case, q, 7)
     _, Jw = oracle_lib.rhs_jvp(P, q, w)
     qb = S.rhs_vjp(S.from_interior(q), S.from_interior(v))
     lhs = dot(v, Jw)
@@ -90,7 +91,7 @@ def test_rk3_step_vjp_dot_product(oracle_lib, mfc_lib, cuda_device, name, prec):
     S = solver_for(mfc_lib, case, precision=prec)
     q = oracle_lib.prim_to_cons(P, W)
     dt = oracle_lib.cfl_dt(P, q, case.cfl)
-    w, v = directions(q, 8)
+    w, v = directions(case, q, 8)
     _, Jw = oracle_lib.rk3_step_jvp(P, q, w, dt)
     qb = S.rk3_step_vjp(S.from_interior(q), dt, S.from_interior(v))
     lhs = dot(v, Jw)
@@ -135,8 +136,10 @@ def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi)
 def test_rhs_full_jacobian_workload_states(oracle_lib, mfc_lib, cuda_device, name, weno):
     """Entry by entry on tiny versions of the workloads' initial states
     (stiff interfaces, fluid at rest, sharp jumps), MFC_FP64: the same
-    branches on both sides; entries compared against the largest entry of
-    their own row of J^T."""
+    branches on both sides.  Entries are compared in nondimensional form
+    (each row and column scaled by its field's magnitude), against the
+    largest entry: the volume-fraction rows of a fluid at rest are exactly
+    zero up to rounding on both sides."""
     if name == "water_air":
         case, W = wl.water_air_shock_tube(14)
     elif name == "bubble":
@@ -148,11 +151,14 @@ def test_rhs_full_jacobian_workload_states(oracle_lib, mfc_lib, cuda_device, nam
     S = solver_for(mfc_lib, case)
     q = oracle_lib.prim_to_cons(P, W)
     J, JT = full_jacobians(oracle_lib, S, P, q)
-    rows = np.abs(J).max(axis=1, keepdims=True)
-    rows = np.where(rows > 0, rows, 1.0)
-    rel = np.abs(JT - J) / rows
-    i, j = np.unravel_index(np.argmax(rel), rel.shape)
-    assert rel.max() <= 1e-10, (rel.max(), i, j, J[i, j], JT[i, j])
+    # nondimensional Jacobian D^-1 J D, D = the field scales of every entry of q
+    d = np.repeat(field_scales(case, q), q[0].size)
+    Jn = J * d[None, :] / d[:, None]
+    JTn = JT * d[None, :] / d[:, None]
+    err = np.abs(JTn - Jn) / np.abs(Jn).max()
+    i, j = np.unravel_index(np.argmax(err), err.shape)
+    ncell = q[0].size
+    assert err.max() <= 1e-12, (err.max(), (i // ncell, i % ncell), (j // ncell, j % ncell), J[i, j], JT[i, j])
 
 
 @pytest.mark.parametrize("name", ["smooth_3d_mixed_bc", "smooth_2d_periodic"])
@@ -163,7 +169,7 @@ def test_rk3_step_vjp_central_differences(mfc_lib, cuda_device, name):
     q = S.prim_to_cons(S.from_interior(W))
     dt = S.compute_dt(q)
     qi = S.interior(q).cpu().numpy()
-    w, v = directions(qi, 3)
+    w, v = directions(case, qi, 3)
     w = S.from_interior(w)
     v = S.from_interior(v)
     qb = S.rk3_step_vjp(q, dt, v)
@@ -174,7 +180,7 @@ def test_rk3_step_vjp_central_differences(mfc_lib, cuda_device, name):
         S.rk3_step(qp, dt)
         S.rk3_step(qm, dt)
         fd = float((S.interior(v) * (S.interior(qp) - S.interior(qm))).sum()) / (2 * h)
-        if abs(fd - ad) <= 1e-6 * abs(ad):
+        if abs(fd - ad) <= 1e-5 * abs(ad):
             return
     raise AssertionError((ad, fd))
 
@@ -186,7 +192,7 @@ def test_mixed_precision_adjoint_dot_product(oracle_lib, mfc_lib, cuda_device):
     S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_MIXED)
     q = oracle_lib.prim_to_cons(P, W)
     dt = oracle_lib.cfl_dt(P, q, case.cfl)
-    w, v = directions(q, 9)
+    w, v = directions(case, q, 9)
     _, Jw = oracle_lib.rk3_step_jvp(P, q, w, dt)
     qb = S.rk3_step_vjp(S.from_interior(q), dt, S.from_interior(v))
     assert dot(to_host(S, qb), w) == pytest.approx(dot(v, Jw), rel=1e-4)
