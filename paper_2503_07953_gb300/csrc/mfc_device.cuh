@@ -63,14 +63,33 @@ template <class R> __device__ __forceinline__ R coef_h(const Consts& C, int i);
 template <> __device__ __forceinline__ double coef_h<double>(const Consts& C, int i) { return C.h[i]; }
 template <> __device__ __forceinline__ float coef_h<float>(const Consts& C, int i) { return C.hf[i]; }
 
-// Reciprocal and quotient: IEEE in float64; the fast approximate
-// instruction in float32 (the float32 path is the reduced-precision mode).
+// Reciprocal: in float64 the hardware approximation refined by two
+// Newton-Raphson steps r <- r + r (1 - x r) (each step squares the
+// relative error; the result is within a few ulps, not correctly rounded);
+// in float32 the fast approximate instruction.
+__device__ __forceinline__ double rcp_nr(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 template <class R> __device__ __forceinline__ R rcp(R x);
-template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
-template <class R> __device__ __forceinline__ R quot(R a, R b);
-template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
-template <> __device__ __forceinline__ float quot<float>(float a, float b) { return __fdividef(a, b); }
+
+// Quotient by arithmetic mode: MODE_EXACT IEEE division; MODE_FAST a times
+// the refined reciprocal of b; MODE_MIXED the fast float32 division.
+template <int MODE> struct Arith {
+    static __device__ __forceinline__ double quot(double a, double b) { return a * rcp_nr(b); }
+};
+template <> struct Arith<MODE_EXACT> {
+    static __device__ __forceinline__ double quot(double a, double b) { return a / b; }
+};
+template <> struct Arith<MODE_MIXED> {
+    static __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+};
 
 // Mixture rules (Sec. 2.1.1) with the stiffened-gas EOS (Sec. 2.2):
 // Gamma = sum alpha_i/(gamma_i - 1), Pi = sum alpha_i gamma_i pi_i/(gamma_i - 1),
@@ -110,7 +129,7 @@ __device__ __forceinline__ void cons_to_prim(const double* q, double* w, const C
             u2 = u2 + w[L::MOM + d] * w[L::MOM + d];
         }
     } else {
-        const double irho = 1.0 / rho;
+        const double irho = rcp_nr(rho);
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
             w[L::MOM + d] = q[L::MOM + d] * irho;
@@ -122,7 +141,7 @@ __device__ __forceinline__ void cons_to_prim(const double* q, double* w, const C
     double Gamma, Pi;
     mixture<NF, double>(q + L::A, C, Gamma, Pi);
     const double ke = 0.5 * rho * u2;
-    w[L::E] = (q[L::E] - ke - Pi) / Gamma;
+    w[L::E] = Arith<MODE>::quot(q[L::E] - ke - Pi, Gamma);
 }
 
 // Primitive state of one cell in the precision of the reconstruction.
@@ -346,9 +365,10 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
 // velocity uf (u^{(x)} of Sec. 3.2.1) is u_K outside the fan and S* inside;
 // the volume-fraction slots receive alpha_K uf.  bad is set when a squared
 // sound speed is not positive.
-template <int NF, int ND, int DIR, class R>
+template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
 __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, R* F, R& uf, bool& bad) {
     using L = Lay<NF, ND>;
+    using A = Arith<MODE>;
     R rho[2], un[2], p[2], E[2], c[2];
 #pragma unroll
     for (int K = 0; K < 2; ++K) {
@@ -365,7 +385,7 @@ __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, 
         un[K] = w[L::MOM + DIR];
         p[K] = w[L::E];
         E[K] = Gamma * p[K] + Pi + R(0.5) * r * u2;
-        const R c2 = quot<R>((Gamma + R(1)) * p[K] + Pi, Gamma * r);
+        const R c2 = A::quot((Gamma + R(1)) * p[K] + Pi, Gamma * r);
         bad |= !(c2 > R(0));
         c[K] = sqrt(c2);
     }
@@ -373,7 +393,7 @@ __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, 
     const R SL = (aR < aL) ? aR : aL;
     const R bL = un[0] + c[0], bR = un[1] + c[1];
     const R SR = (bR > bL) ? bR : bL;
-    const R Ss = quot<R>(p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]),
+    const R Ss = A::quot(p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]),
                          rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
 
     const bool left = Ss >= R(0);
@@ -394,7 +414,7 @@ __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, 
     }
     F[L::E] = (EK + pK) * uK;
     if (star) {
-        const R chi = quot<R>(SK - uK, SK - Ss);
+        const R chi = A::quot(SK - uK, SK - Ss);
 #pragma unroll
         for (int i = 0; i < NF; ++i) {
             const R Us = chi * w[i];
@@ -405,7 +425,7 @@ __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, 
             const R Us = chi * rK * (e == DIR ? Ss : w[L::MOM + e]);
             F[L::MOM + e] = F[L::MOM + e] + SK * (Us - rK * w[L::MOM + e]);
         }
-        const R Es = chi * rK * (quot<R>(EK, rK) + (Ss - uK) * (Ss + quot<R>(pK, rK * (SK - uK))));
+        const R Es = chi * rK * (A::quot(EK, rK) + (Ss - uK) * (Ss + A::quot(pK, rK * (SK - uK))));
         F[L::E] = F[L::E] + SK * (Es - EK);
         uf = Ss;
     } else {

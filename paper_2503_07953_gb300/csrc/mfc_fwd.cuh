@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
                 }
             }
             R F[NQ], uf;
-            hllc<NF, ND, DIR, R>(WLprev, WRm, C, F, uf, bad);
+            hllc<NF, ND, DIR, MODE>(WLprev, WRm, C, F, uf, bad);
             if (m >= s0 + 1) {
                 // finish cell m - 1 = window slot 1: faces m - 3/2 (Fprev) and m - 1/2 (F)
                 const int64_t off = base + (m - 1) * S;

@@ -67,6 +67,25 @@ class Case:
         return (self.hi[a] - self.lo[a]) / self.n[a]
 
 
+def reduced_units(case: Case, W: np.ndarray, rho0: float, p0: float) -> tuple:
+    """The same flow in reduced units: densities over rho0, pressures and
+    pi_inf over p0, velocities over u0 = sqrt(p0 / rho0) (lengths unchanged,
+    so times scale by u0).  The Euler equations with the stiffened-gas EOS
+    are invariant under this change of units; the WENO eps, an absolute
+    constant, is not, and in reduced units it sits far above the rounding
+    size of the smoothness indicators of O(1) fields.  Returns a new
+    (case, W)."""
+    u0 = math.sqrt(p0 / rho0)
+    nf, nd = case.nf, case.ndim
+    W = np.array(W, dtype=np.float64, copy=True)
+    W[:nf] /= rho0
+    W[nf:nf + nd] /= u0
+    W[nf + nd] /= p0
+    out = Case(case.name, list(case.n), list(case.lo), list(case.hi), list(case.bc_lo), list(case.bc_hi),
+               list(case.gamma), [x / p0 for x in case.pi_inf], case.cfl, case.steps, case.weno, case.eps)
+    return out, W
+
+
 def _centres(case: Case):
     """Cell-centre coordinate arrays broadcastable to (nz, ny, nx)."""
     n3 = list(case.n) + [1] * (3 - case.ndim)

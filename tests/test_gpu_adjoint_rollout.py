@@ -8,7 +8,7 @@ import torch
 
 from paper_2503_07953_gb300 import adjoint as adj
 from paper_2503_07953_gb300 import workloads as wl
-from tests.helpers import solver_for
+from tests.helpers import oracle_problem, solver_for, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -49,13 +49,10 @@ def test_checkpointed_gradient_equals_store_all(mfc_lib, cuda_device):
     assert st1.max_live_snapshots <= 3 and st1.advances > st2.advances
 
 
-@pytest.mark.parametrize("precision,tol,h", [(0, 1e-5, 1e-5), (1, 1e-2, 1e-3)])
-def test_wall_impulse_gradient_central_differences(mfc_lib, cuda_device, precision, tol, h):
-    """dJ/d alpha_1(t=0) through the initial-condition map on a 32x32 grid:
-    100 steps (the collapse's pressure waves reach the x = 1 wall), four
-    seeded directions supported where 1e-3 < alpha_1 < 1 - 1e-3, against
-    central differences with the dt sequence held fixed.  The float32 path
-    uses a larger step h so that the difference rises above its rounding."""
+def wall_impulse_setup(mfc_lib, precision):
+    """32x32 bubble collapse, 100 steps (the collapse's pressure waves reach
+    the x = 1 wall), the dt sequence of the forward run held fixed, and the
+    adjoint gradient dJ/d alpha_1(t=0) through the initial-condition map."""
     case, W, S, a1 = setup(mfc_lib, dims=(32, 32), precision=precision)
     nsteps = 100
     q0 = adj.alpha_to_state(S, case, W, a1).detach()
@@ -64,21 +61,54 @@ def test_wall_impulse_gradient_central_differences(mfc_lib, cuda_device, precisi
     J, gq, _, _ = adj.rollout_gradient(S, q0, nsteps, loss, 6, dts)
     a = a1.clone().requires_grad_(True)
     (adj.alpha_to_state(S, case, W, a) * gq).sum().backward()
-    ga = a.grad
+    return case, W, S, a1, dts, loss, a.grad
+
+
+def seeded_directions(a1, count=4):
+    """Seeded directions supported where 1e-3 < alpha_1 < 1 - 1e-3, max-normalised."""
+    band = ((a1 > 1e-3) & (a1 < 1 - 1e-3)).double()
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    for _ in range(count):
+        d = torch.randn(a1.shape, generator=gen, dtype=torch.float64).to(a1.device) * band
+        yield d / float(d.abs().max())
+
+
+def test_wall_impulse_gradient_matches_oracle_forward_mode(oracle_lib, mfc_lib, cuda_device):
+    """The checkpointed reverse sweep (MFC_FP64) against the oracle's
+    forward-mode derivative of the same 100 steps at the same dts: two
+    evaluation orders of one derivative of one floating-point map."""
+    case, W, S, a1, dts, loss, ga = wall_impulse_setup(mfc_lib, 0)
+    P = oracle_problem(oracle_lib, case)
+    for d in seeded_directions(a1):
+        q0, dq0 = torch.func.jvp(lambda x: adj.alpha_to_state(S, case, W, x), (a1,), (d,))
+        q, dq = to_host(S, q0), to_host(S, dq0)
+        fwd = 0.0
+        for n in range(len(dts)):
+            q, dq = oracle_lib.rk3_step_jvp(P, q, dq, dts[n])
+            fwd += float(torch.func.jvp(lambda x: loss(n, x), (S.from_interior(q),), (S.from_interior(dq),))[1])
+        ad = float((ga * d).sum())
+        assert ad == pytest.approx(fwd, rel=1e-9), (ad, fwd)
+
+
+@pytest.mark.parametrize("precision,tol,h", [(0, 1e-5, 1e-6), (1, 1e-2, 1e-3)])
+def test_wall_impulse_gradient_central_differences(mfc_lib, cuda_device, precision, tol, h):
+    """Central differences of J along four seeded directions.  The map is
+    only piecewise smooth (weight and HLLC switches), so the float64
+    difference needs a small step: on this problem the oracle's own
+    differences reach its forward-mode derivative to ~5e-4 at h = 1e-5 and
+    ~2e-6 at h = 1e-6.  The float32 path uses a larger step so that the
+    difference rises above its rounding."""
+    case, W, S, a1, dts, loss, ga = wall_impulse_setup(mfc_lib, precision)
 
     def J_of(alpha):
         q = adj.alpha_to_state(S, case, W, alpha).detach()
         tot = 0.0
-        for n in range(nsteps):
+        for n in range(len(dts)):
             S.rk3_step(q, dts[n])
             tot += float(loss(n, q))
         return tot
 
-    band = ((a1 > 1e-3) & (a1 < 1 - 1e-3)).double()
-    gen = torch.Generator(device="cpu").manual_seed(0)
-    for k in range(4):
-        d = torch.randn(a1.shape, generator=gen, dtype=torch.float64).to(a1.device) * band
-        d = d / float(d.abs().max())
+    for k, d in enumerate(seeded_directions(a1)):
         fd = (J_of(a1 + h * d) - J_of(a1 - h * d)) / (2 * h)
         ad = float((ga * d).sum())
-        assert ad == pytest.approx(fd, rel=tol), (k, ad, fd, J)
+        assert ad == pytest.approx(fd, rel=tol), (k, ad, fd)

@@ -207,6 +207,39 @@ def test_axis_permutation_3d(oracle_lib):
         assert np.abs(pa[k] - b[k]).max() <= 1e-13 * np.abs(pa[k]).max()
 
 
+@pytest.mark.parametrize("name", ["water_air", "bubble_collapse", "stiff_smooth"])
+def test_change_of_units(oracle_lib, name):
+    """Dimensional homogeneity (Sec. 2.1.1 with the stiffened-gas closure):
+    dividing densities by rho0, pressures and pi_inf by p0 and velocities by
+    u0 = sqrt(p0 / rho0) divides each right-hand side by its field's unit
+    times u0 (unit length), and the CFL step is multiplied by u0.  A term with
+    the wrong power of rho, u or p (a dropped density, u where u^2 belongs,
+    sqrt(rho) for rho in the sound speed) breaks it; dimensionless factors
+    are pinned elsewhere.  The mapped weights with eps = 1e-40 are
+    unit-free wherever beta is above rounding size; on flat stencils the
+    candidates agree to rounding, so the edge values do too."""
+    if name == "water_air":
+        case, W = wl.water_air_shock_tube(60); rho0, p0 = 1000.0, 1e9
+    elif name == "bubble_collapse":
+        case, W = wl.bubble_collapse_2d(dims=(24, 22)); rho0, p0 = 1000.0, 1e7
+    else:
+        case = wl.Case("s", [13, 11], [0, 0], [1.0, 0.9], [0, 2], [0, 1], [4.4, 1.4], [6e8, 0.0], 0.4, 0)
+        W = wl.random_smooth_state(case, seed=4, amp=0.15)
+        W[0] *= 1000.0; W[1] *= 50.0; W[2:4] *= 300.0; W[4] *= 1e9
+        rho0, p0 = 997.0, 3.1e8
+    case2, W2 = wl.reduced_units(case, W, rho0, p0)
+    P, P2 = problem(oracle_lib, case), problem(oracle_lib, case2)
+    q, q2 = oracle_lib.prim_to_cons(P, W), oracle_lib.prim_to_cons(P2, W2)
+    L, L2 = oracle_lib.rhs(P, q), oracle_lib.rhs(P2, q2)
+    u0 = math.sqrt(p0 / rho0)
+    nf, nd = case.nf, case.ndim
+    unit = np.array([rho0] * nf + [rho0 * u0] * nd + [p0] + [1.0] * (nf - 1))
+    for k in range(case.nq):
+        scale = np.abs(L[k]).max()
+        assert np.abs(L2[k] * unit[k] * u0 - L[k]).max() <= 1e-11 * scale, k
+    assert oracle_lib.cfl_dt(P2, q2, 0.4) == pytest.approx(oracle_lib.cfl_dt(P, q, 0.4) * u0, rel=1e-13)
+
+
 def test_cfl_dt_closed_form(oracle_lib):
     """Uniform single-fluid state: dt = CFL dx / (|u| + c), c^2 = gamma p / rho."""
     case = wl.Case("d", [10, 5], [0, 0], [2.0, 0.5], [1, 1], [1, 1], [1.4], [0.0], 0.4, 0)
