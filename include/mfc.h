@@ -71,12 +71,14 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   multiply-add, so results are reproducible bit for bit (and equal to a
  *   plain CPU evaluation of the same formulas).
  * MFC_FP64_FAST: float64 with the WENO weight divisions folded into one
- *   reciprocal per normalisation and fused multiply-adds; agrees with
+ *   reciprocal per normalisation, other divisions as products with a
+ *   reciprocal refined to a few ulps, and fused multiply-adds; agrees with
  *   MFC_FP64 to rounding.
  * MFC_MIXED: WENO5 reconstruction, HLLC and the per-direction flux
- *   difference in float32; conservative-to-primitive conversion, the sum
- *   over directions, the Runge-Kutta stage update and the CFL reduction in
- *   float64. */
+ *   differences (and their sum over directions) in float32; the
+ *   cancelling part of the conservative-to-primitive conversion, the
+ *   Runge-Kutta stage update and the CFL reduction in float64 (the CFL
+ *   reduction with the MFC_FP64_FAST arithmetic). */
 typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2 } mfc_precision;
 
 /* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2). */
@@ -131,8 +133,11 @@ mfc_status mfc_prim_to_cons(mfc_ctx* ctx, const double* w, double* q, void* stre
 /* Conservative -> primitive: p = (rho E - 1/2 rho |u|^2 - Pi)/Gamma. */
 mfc_status mfc_cons_to_prim(mfc_ctx* ctx, const double* q, double* w, void* stream);
 
-/* CFL time step of state q.  dt_out is a HOST pointer; the call synchronises
- * the stream and returns MFC_ERR_NONPHYSICAL if the flag was set. */
+/* CFL time step of state q: CFL * min over cells and axes of
+ * dx_d / (|u_d| + c), in the context's float64 arithmetic (MFC_FP64: the
+ * formula as written, bit for bit).  dt_out is a HOST pointer; the call
+ * synchronises the stream and returns MFC_ERR_NONPHYSICAL if the flag was
+ * set. */
 mfc_status mfc_compute_dt(mfc_ctx* ctx, const double* q, double* dt_out, void* stream);
 
 /* rhs = L(q) on every interior cell (Eq. (rhs)). */

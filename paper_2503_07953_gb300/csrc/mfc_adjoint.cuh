@@ -10,29 +10,55 @@
 
 namespace mfc {
 
+// Division by one denominator b, possibly several times: IEEE a / b in
+// MODE_EXACT; a times one reciprocal of b otherwise (rcp<R>).  div2 divides
+// by b^2.  Only the reverse (bar) arithmetic and forward quantities that
+// decide no branch go through it; the forward values that pick a branch
+// (wave speeds, S*, the fallback test) are recomputed with the forward
+// pass's own arithmetic.
+template <int MODE, class R>
+struct Recip {
+    R b, ib;
+    __device__ __forceinline__ explicit Recip(R x) : b(x) {
+        if constexpr (MODE == MODE_EXACT) ib = R(0);
+        else ib = rcp<R>(x);
+    }
+    __device__ __forceinline__ R div(R a) const {
+        if constexpr (MODE == MODE_EXACT) return a / b;
+        else return a * ib;
+    }
+    __device__ __forceinline__ R div2(R a) const {
+        if constexpr (MODE == MODE_EXACT) return a / (b * b);
+        else return a * ib * ib;
+    }
+};
+
 // q_bar += (dW/dq)^T W_bar for the conservative state q of one cell.
-template <int NF, int ND>
+template <int NF, int ND, int MODE = MODE_EXACT>
 __device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* wbar, const Consts& C,
                                                  double* qbar) {
     using L = Lay<NF, ND>;
+    constexpr int M = (MODE == MODE_EXACT) ? MODE_EXACT : MODE_FAST;  // float64 throughout
     double rho = q[0];
 #pragma unroll
     for (int i = 1; i < NF; ++i) rho = rho + q[i];
+    const Recip<M, double> rr(rho);
     double u[ND];
     double u2 = 0.0;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        u[d] = q[L::MOM + d] / rho;
+        u[d] = rr.div(q[L::MOM + d]);
         u2 = u2 + u[d] * u[d];
     }
     double Gamma, Pi;
     mixture<NF, double>(q + L::A, C, Gamma, Pi);
+    const Recip<M, double> rg(Gamma);
     const double ke = 0.5 * rho * u2;
-    const double p = (q[L::E] - ke - Pi) / Gamma;
+    const double p = rg.div(q[L::E] - ke - Pi);
     // p = (E - ke - Pi) / Gamma
     const double pb = wbar[L::E];
-    const double numb = pb / Gamma;
-    const double Gb = -pb * p / Gamma;
+    const double numb = rg.div(pb);
+    const double Gb = rg.div(-pb * p);
     const double Pb = -numb;
     qbar[L::E] += numb;
     const double keb = -numb;
@@ -41,8 +67,8 @@ __device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* 
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         const double ub = wbar[L::MOM + d] + u2b * 2.0 * u[d];
-        qbar[L::MOM + d] += ub / rho;
-        rhob -= ub * u[d] / rho;
+        qbar[L::MOM + d] += rr.div(ub);
+        rhob -= rr.div(ub * u[d]);
     }
 #pragma unroll
     for (int i = 0; i < NF; ++i) qbar[i] += wbar[i] + rhob;
@@ -54,40 +80,58 @@ __device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* 
 // Adjoint of the nonlinear weights and the final sum of one edge:
 // given p[3], beta[3], ideal weights d[3] and out_bar, add to p_bar and
 // beta_bar.
-template <class R>
+template <int MODE, class R>
 __device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const R* d, int variant, R eps, R outb,
                                                R* pb, R* betab) {
-    R a[3], w[3], t[3];
+    R a[3], w[3], t[3], it[3];
     R tau = R(0);
     if (variant == WENO_Z) {
         tau = fabs(beta[0] - beta[2]);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) a[r] = d[r] * (R(1) + tau / (beta[r] + eps));
+        for (int r = 0; r < 3; ++r) {
+            t[r] = beta[r] + eps;
+            const Recip<MODE, R> rt(t[r]);
+            it[r] = rt.ib;
+            a[r] = d[r] * (R(1) + rt.div(tau));
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             t[r] = eps + beta[r];
-            a[r] = d[r] / (t[r] * t[r]);
+            const Recip<MODE, R> rt(t[r]);
+            it[r] = rt.ib;
+            a[r] = rt.div2(d[r]);
         }
     }
     const R s = a[0] + a[1] + a[2];
+    const Recip<MODE, R> rs(s);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) w[r] = a[r] / s;
-    R om[3], Nn[3], Dd[3], gm[3], sm = R(1);
+    for (int r = 0; r < 3; ++r) w[r] = rs.div(a[r]);
+    R om[3], Nn[3], Dd[3], iD[3], gm[3];
+    R sm = R(1), ism = R(1);
     if (variant == WENO_M) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             Nn[r] = d[r] + d[r] * d[r] - R(3) * d[r] * w[r] + w[r] * w[r];
             Dd[r] = d[r] * d[r] + w[r] * (R(1) - R(2) * d[r]);
-            gm[r] = w[r] * Nn[r] / Dd[r];
+            const Recip<MODE, R> rd(Dd[r]);
+            iD[r] = rd.ib;
+            gm[r] = rd.div(w[r] * Nn[r]);
         }
         sm = gm[0] + gm[1] + gm[2];
+        const Recip<MODE, R> rsm(sm);
+        ism = rsm.ib;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) om[r] = gm[r] / sm;
+        for (int r = 0; r < 3; ++r) om[r] = rsm.div(gm[r]);
     } else {
 #pragma unroll
         for (int r = 0; r < 3; ++r) om[r] = w[r];
     }
+    // division by a denominator whose reciprocal was taken above
+    auto dv = [](R a_, R b_, R ib_) -> R {
+        if constexpr (MODE == MODE_EXACT) return a_ / b_;
+        else return a_ * ib_;
+    };
     // out = sum om_r p_r
     R omb[3];
 #pragma unroll
@@ -101,11 +145,15 @@ __device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const 
         const R dot = omb[0] * om[0] + omb[1] * om[1] + omb[2] * om[2];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            const R gb = (omb[r] - dot) / sm;
+            const R gb = dv(omb[r] - dot, sm, ism);
             // gm = w N(w) / D(w), N' = -3 d + 2 w, D' = 1 - 2 d
             const R dN = R(-3) * d[r] + R(2) * w[r];
             const R dD = R(1) - R(2) * d[r];
-            const R dg = (Nn[r] + w[r] * dN) / Dd[r] - w[r] * Nn[r] * dD / (Dd[r] * Dd[r]);
+            R dg;
+            if constexpr (MODE == MODE_EXACT)
+                dg = (Nn[r] + w[r] * dN) / Dd[r] - w[r] * Nn[r] * dD / (Dd[r] * Dd[r]);
+            else
+                dg = ((Nn[r] + w[r] * dN) - w[r] * Nn[r] * dD * iD[r]) * iD[r];
             wb[r] = gb * dg;
         }
     } else {
@@ -116,27 +164,32 @@ __device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const 
     const R dotw = wb[0] * w[0] + wb[1] * w[1] + wb[2] * w[2];
     R ab[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) ab[r] = (wb[r] - dotw) / s;
+    for (int r = 0; r < 3; ++r) ab[r] = rs.div(wb[r] - dotw);
     if (variant == WENO_Z) {
         R taub = R(0);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            const R be = beta[r] + eps;
-            taub += ab[r] * d[r] / be;
-            betab[r] += -ab[r] * d[r] * tau / (be * be);
+            if constexpr (MODE == MODE_EXACT) {
+                const R be = beta[r] + eps;
+                taub += ab[r] * d[r] / be;
+                betab[r] += -ab[r] * d[r] * tau / (be * be);
+            } else {
+                taub += ab[r] * d[r] * it[r];
+                betab[r] += -ab[r] * d[r] * tau * it[r] * it[r];
+            }
         }
         const R sg = (beta[0] - beta[2] >= R(0)) ? R(1) : R(-1);
         betab[0] += taub * sg;
         betab[2] -= taub * sg;
     } else {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) betab[r] += ab[r] * (R(-2) * a[r] / t[r]);
+        for (int r = 0; r < 3; ++r) betab[r] += ab[r] * dv(R(-2) * a[r], t[r], it[r]);
     }
 }
 
 // Adjoint of weno5_cell: given the bars of the right-edge value (vrb) and
 // the left-edge value (vlb), add df to fb[0..4].
-template <class R>
+template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R* fb) {
     const R c13 = R(13.0 / 12.0), c14 = R(0.25);
     const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
@@ -149,13 +202,17 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
     weno5_scaled_beta(f[0], f[1], f[2], f[3], f[4], eps, beta, e, scale);
     R betab[3] = {R(0), R(0), R(0)};
     const R sixth = R(1) / R(6);
+    auto by6 = [&](R x) -> R {
+        if constexpr (MODE == MODE_EXACT) return x / R(6);
+        else return x * sixth;
+    };
     if (vrb != R(0)) {
         R p[3], pb[3] = {R(0), R(0), R(0)};
         const R d[3] = {R(0.1), R(0.6), R(0.3)};
-        p[0] = (R(2) * f[0] - R(7) * f[1] + R(11) * f[2]) / R(6);
-        p[1] = (-f[1] + R(5) * f[2] + R(2) * f[3]) / R(6);
-        p[2] = (R(2) * f[2] + R(5) * f[3] - f[4]) / R(6);
-        weno5_edge_adj(p, beta, d, variant, e, vrb, pb, betab);
+        p[0] = by6(R(2) * f[0] - R(7) * f[1] + R(11) * f[2]);
+        p[1] = by6(-f[1] + R(5) * f[2] + R(2) * f[3]);
+        p[2] = by6(R(2) * f[2] + R(5) * f[3] - f[4]);
+        weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vrb, pb, betab);
         fb[0] += (R(2) * pb[0]) * sixth;
         fb[1] += (R(-7) * pb[0] - pb[1]) * sixth;
         fb[2] += (R(11) * pb[0] + R(5) * pb[1] + R(2) * pb[2]) * sixth;
@@ -165,10 +222,10 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
     if (vlb != R(0)) {
         R p[3], pb[3] = {R(0), R(0), R(0)};
         const R d[3] = {R(0.3), R(0.6), R(0.1)};
-        p[0] = (-f[0] + R(5) * f[1] + R(2) * f[2]) / R(6);
-        p[1] = (R(2) * f[1] + R(5) * f[2] - f[3]) / R(6);
-        p[2] = (R(11) * f[2] - R(7) * f[3] + R(2) * f[4]) / R(6);
-        weno5_edge_adj(p, beta, d, variant, e, vlb, pb, betab);
+        p[0] = by6(-f[0] + R(5) * f[1] + R(2) * f[2]);
+        p[1] = by6(R(2) * f[1] + R(5) * f[2] - f[3]);
+        p[2] = by6(R(11) * f[2] - R(7) * f[3] + R(2) * f[4]);
+        weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vlb, pb, betab);
         fb[0] += (-pb[0]) * sixth;
         fb[1] += (R(5) * pb[0] + R(2) * pb[1]) * sixth;
         fb[2] += (R(2) * pb[0] + R(5) * pb[1] + R(11) * pb[2]) * sixth;
@@ -191,10 +248,11 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
 
 // Adjoint of hllc: given F_bar[NQ] and uf_bar, add to WLb, WRb.
 // Also returns the forward face velocity in uf_out.
-template <int NF, int ND, int DIR, class R>
+template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
 __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts& C, const R* Fb, R ufb, R* WLb,
                                          R* WRb, R& uf_out) {
     using L = Lay<NF, ND>;
+    using Q = Arith<MODE>;
     constexpr int NQ = L::NQ;
     // ---- forward recomputation ----
     R rho[2], un[2], p[2], E[2], c[2], G[2], P[2], u2[2], c2[2];
@@ -213,7 +271,7 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
         un[K] = w[L::MOM + DIR];
         p[K] = w[L::E];
         E[K] = G[K] * p[K] + P[K] + R(0.5) * r * s2;
-        c2[K] = ((G[K] + R(1)) * p[K] + P[K]) / (G[K] * r);
+        c2[K] = Q::quot((G[K] + R(1)) * p[K] + P[K], G[K] * r);
         c[K] = sqrt(c2[K]);
     }
     const R aL = un[0] - c[0], aR = un[1] - c[1];
@@ -224,7 +282,7 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
     const R SR = maxR ? bR : bL;
     const R num = p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]);
     const R den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
-    const R Ss = num / den;
+    const R Ss = Q::quot(num, den);
     const bool left = Ss >= R(0);
     const int K = left ? 0 : 1;
     const R* w = left ? WL : WR;
@@ -249,12 +307,14 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
     if (star) {
         Ssb += ufb_t;
         const R A = SK - uK, B = SK - Ss;
-        const R chi = A / B;
+        const R chi = Q::quot(A, B);
+        const Recip<MODE, R> rB(B), rK_(rK);
         R chib = R(0);
         // energy
         const R Z = rK * (SK - uK);
-        const R Y = Ss + pK / Z;
-        const R X = EK / rK + (Ss - uK) * Y;
+        const Recip<MODE, R> rZ(Z);
+        const R Y = Ss + rZ.div(pK);
+        const R X = rK_.div(EK) + (Ss - uK) * Y;
         const R Es = chi * rK * X;
         SKb += Fb[L::E] * (Es - EK);
         const R Esb = Fb[L::E] * SK;
@@ -262,14 +322,14 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
         chib += Esb * rK * X;
         rKb += Esb * chi * X;
         const R Xb = Esb * chi * rK;
-        EKb += Xb / rK;
-        rKb -= Xb * EK / (rK * rK);
+        EKb += rK_.div(Xb);
+        rKb -= rK_.div2(Xb * EK);
         Ssb += Xb * Y;
         uKb -= Xb * Y;
         const R Yb = Xb * (Ss - uK);
         Ssb += Yb;
-        pKb += Yb / Z;
-        const R Zb = -Yb * pK / (Z * Z);
+        pKb += rZ.div(Yb);
+        const R Zb = rZ.div2(-Yb * pK);
         rKb += Zb * (SK - uK);
         SKb += Zb * rK;
         uKb -= Zb * rK;
@@ -297,8 +357,8 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
             wb[i] += Fb[i] * SK * (chi - R(1));
         }
         // chi = A / B
-        const R Ab = chib / B;
-        const R Bb = -chib * chi / B;
+        const R Ab = rB.div(chib);
+        const R Bb = rB.div(-chib * chi);
         SKb += Ab + Bb;
         uKb -= Ab;
         Ssb -= Bb;
@@ -333,8 +393,9 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
     R SLb = left ? SKb : R(0);
     R SRb = left ? R(0) : SKb;
     // Ss = num / den
-    const R numb = Ssb / den;
-    const R denb = -Ssb * Ss / den;
+    const Recip<MODE, R> rden(den);
+    const R numb = rden.div(Ssb);
+    const R denb = rden.div(-Ssb * Ss);
     pb[1] += numb;
     pb[0] -= numb;
     rb[0] += numb * un[0] * (SL - un[0]);
@@ -376,10 +437,11 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
         const R* ws = S ? WR : WL;
         R* o = outs[S];
         // c = sqrt(c2), c2 = ((G + 1) p + P) / (G r)
-        const R c2b = cb[S] / (R(2) * c[S]);
+        const R c2b = Recip<MODE, R>(R(2) * c[S]).div(cb[S]);
         const R Dd = G[S] * rho[S];
-        const R Nnb = c2b / Dd;
-        const R Ddb = -c2b * c2[S] / Dd;
+        const Recip<MODE, R> rDd(Dd);
+        const R Nnb = rDd.div(c2b);
+        const R Ddb = rDd.div(-c2b * c2[S]);
         R Gb = Nnb * p[S] + Ddb * rho[S];
         R Pb = Nnb;
         R pbs = pb[S] + Nnb * (G[S] + R(1));

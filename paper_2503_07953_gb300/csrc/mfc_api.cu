@@ -210,7 +210,7 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
     set_scalars_kernel<<<1, 1, 0, s>>>(ctx->scal, dt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "set scalars");
     if (dt > 0.0) return MFC_OK;
-    if ((e = ctx->exact->cfl(ctx->C, q, &ctx->scal->minbits, &ctx->scal->flag, s)) != cudaSuccess)
+    if ((e = ctx->fns->cfl(ctx->C, q, &ctx->scal->minbits, &ctx->scal->flag, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "cfl kernel");
     finalize_dt_kernel<<<1, 1, 0, s>>>(ctx->scal, ctx->C.cfl, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "finalize dt");
@@ -218,17 +218,22 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
 }
 
 // All directional sweeps of one evaluation of L(qin).  out_kind 0 writes
-// L into rhs; 1 and 2 fuse the RK stage update into the last sweep.
+// L into rhs; 1 and 2 fuse the RK stage update into the last sweep.  The
+// mixed mode sums the directions in a float accumulator that aliases the
+// scratch buffer ctx->r (first half; rhs may be ctx->r itself only when
+// out_kind is 1 or 2, where rhs is not written).
 mfc_status eval_L(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, const double* qn, double* qout,
                   double a, double b, cudaStream_t s) {
+    const bool mixed = ctx->mode == mfc::MODE_MIXED;
     for (int d = 0; d < ctx->C.nd; ++d) {
         mfc::SweepArgs A;
         std::memset(&A, 0, sizeof(A));
         A.q = qin;
         A.rhs = rhs;
-        A.acc_in = d > 0;
+        A.rhsf = reinterpret_cast<float*>(ctx->r);
         const bool last = d == ctx->C.nd - 1;
-        A.out_kind = last ? out_kind : 0;
+        A.acc_in = d == 0 ? 0 : (mixed ? 2 : 1);
+        A.out_kind = last ? out_kind : (mixed ? 3 : 0);
         A.qn = qn;
         A.qout = qout;
         A.dt = &ctx->scal->dt;

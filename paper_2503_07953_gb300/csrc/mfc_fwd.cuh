@@ -20,7 +20,7 @@ namespace mfc {
 // state of a face is not a physical mixture, the face uses the states of
 // its two cells (first-order reconstruction) instead.
 template <int NF, int ND, int DIR, int MODE>
-__global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepArgs A) {
+__device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) {
     using L = Lay<NF, ND>;
     using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
@@ -95,7 +95,17 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
                         if (k >= L::A) t = t + W[1][k] * du * inv_dx;
                     }
                     const int64_t o = off + k * C.fstride;
-                    const double Lc = A.acc_in ? A.rhs[o] + double(t) : double(t);
+                    double Lc;
+                    if constexpr (MODE == MODE_MIXED) {
+                        const float Lf = (A.acc_in == 2) ? A.rhsf[o] + t : t;
+                        if (A.out_kind == 3) {
+                            A.rhsf[o] = Lf;
+                            continue;
+                        }
+                        Lc = double(Lf);
+                    } else {
+                        Lc = A.acc_in ? A.rhs[o] + double(t) : double(t);
+                    }
                     if (A.out_kind == 0) {
                         A.rhs[o] = Lc;
                     } else if (A.out_kind == 1) {
@@ -117,6 +127,18 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepA
             for (int k = 0; k < NQ; ++k) W[s][k] = W[s + 1][k];
     }
     if (bad) atomicOr(A.flag, 1);
+}
+
+template <int NF, int ND, int DIR, int MODE>
+__global__ void __launch_bounds__(128) sweep_kernel(const Consts C, const SweepArgs A) {
+    sweep_body<NF, ND, DIR, MODE>(C, A);
+}
+
+// The mixed mode fits in 128 registers without spilling: four blocks per SM
+// (16 warps) hide more of the latency of its float64 steps.
+template <int NF, int ND, int DIR>
+__global__ void __launch_bounds__(128, 4) sweep_kernel_mixed(const Consts C, const SweepArgs A) {
+    sweep_body<NF, ND, DIR, MODE_MIXED>(C, A);
 }
 
 // Interior linear index -> element offset in the padded layout.
@@ -160,6 +182,69 @@ __global__ void __launch_bounds__(256) cfl_kernel(const Consts C, const double* 
             const double s = C.dx[d] / (fabs(w[L::MOM + d]) + cs);
             m = (s < m) ? s : m;
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_down_sync(0xffffffffu, m, o);
+        m = (t < m) ? t : m;
+    }
+    __shared__ double wm[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wm[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        m = (lane < (int)(blockDim.x >> 5)) ? wm[lane] : __longlong_as_double(0x7ff0000000000000ULL);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double t = __shfl_down_sync(0xffffffffu, m, o);
+            m = (t < m) ? t : m;
+        }
+        if (lane == 0) atomicMin(minbits, (unsigned long long)__double_as_longlong(m));
+    }
+    if (bad) atomicOr(flag, 1);
+}
+
+// The CFL reduction in the MODE_FAST arithmetic (MFC_FP64_FAST and
+// MFC_MIXED): one refined reciprocal each for rho, Gamma and the largest
+// (|u_d| + c)/dx_d of the cell, whose reciprocal is min_d dx_d/(|u_d| + c);
+// float64 throughout, same reductions as cfl_kernel.
+template <int NF, int ND>
+__global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const double* q, unsigned long long* minbits,
+                                                       int* flag) {
+    using L = Lay<NF, ND>;
+    constexpr int NQ = L::NQ;
+    const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
+    double m = __longlong_as_double(0x7ff0000000000000ULL);
+    bool bad = false;
+    for (int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lin < ncell;
+         lin += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t off = interior_offset(C, lin);
+        double qc[NQ];
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) qc[f] = __ldg(q + off + f * C.fstride);
+        double rho = qc[0];
+#pragma unroll
+        for (int i = 1; i < NF; ++i) rho = rho + qc[i];
+        bad |= !(rho > 0.0);
+        const double irho = rcp_nr(rho);
+        double u[ND], ke = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            u[d] = qc[L::MOM + d] * irho;
+            ke = fma(qc[L::MOM + d], u[d], ke);
+        }
+        double Gamma, Pi;
+        mixture<NF, double>(qc + L::A, C, Gamma, Pi);
+        const double iG = rcp_nr(Gamma);
+        const double p = (qc[L::E] - 0.5 * ke - Pi) * iG;
+        const double c2 = ((Gamma + 1.0) * p + Pi) * iG * irho;
+        bad |= !(c2 > 0.0);
+        const double cs = sqrt(c2);
+        double smax = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) smax = fmax(smax, (fabs(u[d]) + cs) * C.inv_dx[d]);
+        const double s = rcp_nr(smax);
+        m = (s < m) ? s : m;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

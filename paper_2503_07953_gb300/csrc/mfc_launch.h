@@ -11,13 +11,19 @@
 namespace mfc {
 
 // What the sweep does with its per-direction contribution t of cell c:
-//   acc_in = 0: Lc = t;  acc_in = 1: Lc = rhs[c] + t
+//   acc_in = 0: Lc = t;  acc_in = 1: Lc = rhs[c] + t;  acc_in = 2: Lc = rhsf[c] + t
 //   out_kind = 0: rhs[c] = Lc
 //   out_kind = 1: qout[c] = q[c] + dt Lc                       (RK3 stage 1)
 //   out_kind = 2: qout[c] = rk_a qn[c] + rk_b (q[c] + dt Lc)   (RK3 stages 2, 3)
+//   out_kind = 3: rhsf[c] = Lc
+// The float accumulator (acc_in 2, out_kind 3) carries the sum of the
+// directional contributions between the sweeps of the mixed-precision
+// mode, whose contributions are float32 values; the stage update itself
+// is float64 in every mode.
 struct SweepArgs {
     const double* q;      // stage input (stencil source)
     double* rhs;          // accumulated right-hand side
+    float* rhsf;          // float accumulator (mixed precision)
     const double* qn;     // q^n for out_kind 2 (may alias qout)
     double* qout;         // stage output for out_kind 1, 2
     const double* dt;     // device scalar
@@ -43,9 +49,10 @@ struct LaunchFns {
     cudaError_t (*sweep)(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
     // One directional sweep of the adjoint of L (see mfc_vjp.cuh).
     cudaError_t (*sweep_vjp)(const Consts& C, int dir, int mode, VjpArgs A, cudaStream_t s);
-    // Exact tables only: CFL minimum of dx_d / (|u_d| + c) into *minbits
-    // (atomicMin), and the primitive / conservative maps.
+    // CFL minimum of dx_d / (|u_d| + c) into *minbits (atomicMin), in the
+    // table's float64 arithmetic.
     cudaError_t (*cfl)(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s);
+    // Exact tables only: the primitive / conservative maps.
     cudaError_t (*prim_to_cons)(const Consts& C, const double* w, double* q, cudaStream_t s);
     cudaError_t (*cons_to_prim)(const Consts& C, const double* q, double* w, int* flag, cudaStream_t s);
 };

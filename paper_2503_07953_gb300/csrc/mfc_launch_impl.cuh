@@ -28,7 +28,10 @@ inline unsigned stride_grid(int64_t n, int block) {
 
 template <int NF, int ND, int DIR, int MODE>
 void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream_t s) {
-    sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
+    if constexpr (MODE == MODE_MIXED)
+        sweep_kernel_mixed<NF, ND, DIR><<<grid, kSweepBlock, 0, s>>>(C, A);
+    else
+        sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
 }
 
 template <int NF, int ND, int DIR, int MODE>
@@ -106,10 +109,18 @@ struct Launch {
     static cudaError_t cfl(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s) {
         const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
         const unsigned grid = stride_grid(ncell, 256);
-        switch (C.nd) {
-            case 1: cfl_kernel<NF, 1><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
-            case 2: cfl_kernel<NF, 2><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
-            default: cfl_kernel<NF, 3><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+        if constexpr (EXACT) {
+            switch (C.nd) {
+                case 1: cfl_kernel<NF, 1><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+                case 2: cfl_kernel<NF, 2><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+                default: cfl_kernel<NF, 3><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+            }
+        } else {
+            switch (C.nd) {
+                case 1: cfl_fast_kernel<NF, 1><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+                case 2: cfl_fast_kernel<NF, 2><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+                default: cfl_fast_kernel<NF, 3><<<grid, 256, 0, s>>>(C, q, minbits, flag); break;
+            }
         }
         return cudaGetLastError();
     }
@@ -134,8 +145,7 @@ struct Launch {
         return cudaGetLastError();
     }
     static const LaunchFns& fns() {
-        static const LaunchFns f = {&sweep, &sweep_vjp, EXACT ? &cfl : nullptr, EXACT ? &p2c : nullptr,
-                                    EXACT ? &c2p : nullptr};
+        static const LaunchFns f = {&sweep, &sweep_vjp, &cfl, EXACT ? &p2c : nullptr, EXACT ? &c2p : nullptr};
         return f;
     }
 };

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     ufb += (rbar(j, k) * Wr[j & 7][k] - rbar(j + 1, k) * Wr[(j + 1) & 7][k]) * inv_dx;
                 }
                 R uf;
-                hllc_adj<NF, ND, DIR, R>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
+                hllc_adj<NF, ND, DIR, MODE>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
                 ufr[j & 7] = uf;
                 if (first_order) {
                     // the face states are the cell states themselves
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     R f[5], fb[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
                     for (int m = 0; m < 5; ++m) f[m] = Wr[(j - 2 + m) & 7][k];
-                    weno5_cell_adj<R>(f, WRbprev[k], WLb[k], variant, eps, fb);
+                    weno5_cell_adj<MODE, R>(f, WRbprev[k], WLb[k], variant, eps, fb);
 #pragma unroll
                     for (int m = 0; m < 5; ++m)
                         if (fb[m] != R(0)) sink(j - 2 + m, k, fb[m]);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     wb[k] = v;
                     qb[k] = 0.0;
                 }
-                cons_to_prim_adj<NF, ND>(qc, wb, C, qb);
+                cons_to_prim_adj<NF, ND, MODE>(qc, wb, C, qb);
                 // alpha_c (u_{c+1/2} - u_{c-1/2}) / dx
                 const double du = double(ufr[c & 7]) - double(ufr[(c - 1) & 7]);
 #pragma unroll

@@ -73,11 +73,14 @@ def seeded_directions(a1, count=4):
         yield d / float(d.abs().max())
 
 
-def test_wall_impulse_gradient_matches_oracle_forward_mode(oracle_lib, mfc_lib, cuda_device):
-    """The checkpointed reverse sweep (MFC_FP64) against the oracle's
-    forward-mode derivative of the same 100 steps at the same dts: two
-    evaluation orders of one derivative of one floating-point map."""
-    case, W, S, a1, dts, loss, ga = wall_impulse_setup(mfc_lib, 0)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-3)])
+def test_wall_impulse_gradient_matches_oracle_forward_mode(oracle_lib, mfc_lib, cuda_device, precision, tol):
+    """The checkpointed reverse sweep against the oracle's forward-mode
+    derivative of the same 100 steps at the same dts.  MFC_FP64: two
+    evaluation orders of one derivative of one floating-point map.
+    MFC_MIXED: the float32 reconstruction and Riemann solve perturb the
+    gradient by ~1e-5 relative (measured)."""
+    case, W, S, a1, dts, loss, ga = wall_impulse_setup(mfc_lib, precision)
     P = oracle_problem(oracle_lib, case)
     for d in seeded_directions(a1):
         q0, dq0 = torch.func.jvp(lambda x: adj.alpha_to_state(S, case, W, x), (a1,), (d,))
@@ -87,17 +90,20 @@ def test_wall_impulse_gradient_matches_oracle_forward_mode(oracle_lib, mfc_lib, 
             q, dq = oracle_lib.rk3_step_jvp(P, q, dq, dts[n])
             fwd += float(torch.func.jvp(lambda x: loss(n, x), (S.from_interior(q),), (S.from_interior(dq),))[1])
         ad = float((ga * d).sum())
-        assert ad == pytest.approx(fwd, rel=1e-9), (ad, fwd)
+        assert ad == pytest.approx(fwd, rel=tol), (ad, fwd)
 
 
-@pytest.mark.parametrize("precision,tol,h", [(0, 1e-5, 1e-6), (1, 1e-2, 1e-3)])
+@pytest.mark.parametrize("precision,tol,h", [(0, 1e-5, 1e-6), (1, 5e-2, 1e-3)])
 def test_wall_impulse_gradient_central_differences(mfc_lib, cuda_device, precision, tol, h):
     """Central differences of J along four seeded directions.  The map is
     only piecewise smooth (weight and HLLC switches), so the float64
     difference needs a small step: on this problem the oracle's own
     differences reach its forward-mode derivative to ~5e-4 at h = 1e-5 and
-    ~2e-6 at h = 1e-6.  The float32 path uses a larger step so that the
-    difference rises above its rounding."""
+    ~2e-6 at h = 1e-6.  The float32 path needs a step large enough for the
+    difference to rise above its rounding, where the truncation error of
+    this non-smooth map is itself ~1e-2 (the oracle's float64 differences
+    at h = 1e-3 miss by up to 2.4e-2), so it is a coarse check; the mixed
+    gradient is held to 1e-3 against the oracle's forward mode above."""
     case, W, S, a1, dts, loss, ga = wall_impulse_setup(mfc_lib, precision)
 
     def J_of(alpha):
