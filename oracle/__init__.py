@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
-WENO_JS, WENO_M, WENO_Z = 0, 1, 2
+WENO_JS, WENO_M, WENO_Z, WENO_TENO = 0, 1, 2, 3
 MAXF = 4
 
 _lock = threading.Lock()
@@ -52,7 +52,8 @@ class _Problem(ctypes.Structure):
         ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
         ("bc_lo", ctypes.c_int32 * 3), ("bc_hi", ctypes.c_int32 * 3),
         ("gamma", ctypes.c_double * MAXF), ("pi_inf", ctypes.c_double * MAXF),
-        ("weno", ctypes.c_int32), ("eps", ctypes.c_double),
+        ("weno", ctypes.c_int32), ("eps", ctypes.c_double), ("teno_ct", ctypes.c_double),
+        ("model", ctypes.c_int32),
     ]
 
 
@@ -77,7 +78,7 @@ def _load():
                 "oc_rk3_step_sampled": (ctypes.c_int, [P, dp, ctypes.c_double, ctypes.c_int64, i64p, dp]),
                 "oc_rk3_step_count": (ctypes.c_int, [P, dp, ctypes.c_double, i64p]),
                 "oc_block_counts": (ctypes.c_int, [P, dp, dp, i64p]),
-                "oc_weno5_detail": (None, [ctypes.c_int, ctypes.c_double, dp, dp]),
+                "oc_weno5_detail": (None, [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]),
                 "oc_hllc_face": (ctypes.c_int, [P, ctypes.c_int, dp, dp, dp, dp]),
                 "oc_rk3_linear": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
             }
@@ -101,6 +102,8 @@ class Problem:
     bc_hi: Sequence[int] = None
     weno: int = WENO_M
     eps: float = 1e-40
+    teno_ct: float = 1e-6
+    model: int = 0                        # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -137,7 +140,8 @@ class Problem:
         for i in range(MAXF):
             p.gamma[i] = float(self.gamma[i]) if i < self.nf else 0.0
             p.pi_inf[i] = float(self.pi_inf[i]) if i < self.nf else 0.0
-        p.weno, p.eps = int(self.weno), float(self.eps)
+        p.weno, p.eps, p.teno_ct = int(self.weno), float(self.eps), float(self.teno_ct)
+        p.model = int(self.model)
         return p
 
     def dx(self, axis: int) -> float:
@@ -254,12 +258,12 @@ def block_counts(P: Problem, qa, qb) -> dict:
     return {n: dict(zip(keys, out[i].tolist())) for i, n in enumerate(names)}
 
 
-def weno5_detail(f, variant: int = WENO_M, eps: float = 1e-40) -> dict:
+def weno5_detail(f, variant: int = WENO_M, eps: float = 1e-40, teno_ct: float = 1e-6) -> dict:
     lib = _load()
     f = np.ascontiguousarray(f, dtype=np.float64)
     assert f.shape == (5,)
     out = np.zeros(17)
-    lib.oc_weno5_detail(int(variant), float(eps), _dp(f), _dp(out))
+    lib.oc_weno5_detail(int(variant), float(eps), float(teno_ct), _dp(f), _dp(out))
     return {"p_right": out[0:3].copy(), "beta": out[3:6].copy(), "w_right": out[6:9].copy(),
             "v_right": out[9], "p_left": out[10:13].copy(), "w_left": out[13:16].copy(), "v_left": out[16]}
 

@@ -14,17 +14,19 @@
  *   Cnt     - a double that counts the floating-point operations it performs.
  *
  * What it computes (all citations are to the paper):
- *   * five-equation (Allaire, K = 0) model, Sec. 2.1.1: partial densities
- *     alpha_i rho_i, mixture momentum rho u, total energy rho E and N_f - 1
- *     volume fractions alpha_j, with alpha_N = 1 - sum_j alpha_j (mixture
- *     rules, Sec. 2.1.1);
+ *   * five-equation model, Sec. 2.1.1: partial densities alpha_i rho_i,
+ *     mixture momentum rho u, total energy rho E and N_f - 1 volume
+ *     fractions alpha_j, with alpha_N = 1 - sum_j alpha_j (mixture rules,
+ *     Sec. 2.1.1); K = 0 (Allaire) or, for two fluids, the Kapila K div u
+ *     term with the Wood mixture sound speed;
  *   * stiffened-gas EOS, Sec. 2.2: rho_i e_i = (p + gamma_i pi_i)/(gamma_i - 1),
  *     so rho e = Gamma p + Pi with Gamma = sum alpha_i/(gamma_i - 1) and
  *     Pi = sum alpha_i gamma_i pi_i/(gamma_i - 1);
  *   * finite-volume semi-discretisation, Sec. 3.1, Eq. (rhs), with
  *     h(q) = (0, ..., 0, -alpha) so that the alpha rows get + alpha div(u);
  *   * WENO5 reconstruction of the primitive variables with JS, mapped
- *     (Henrick) and Z weights, Sec. 3.2.1 and Sec. 4.2.2;
+ *     (Henrick) and Z weights, Sec. 3.2.1 and Sec. 4.2.2, and the
+ *     fifth-order TENO stencil selection of Sec. 4.2.2;
  *   * HLLC approximate Riemann solver, Sec. 3.2.2 (Toro's star states);
  *   * ghost cells by periodic wrap, zeroth-order extrapolation or mirror
  *     with negated normal momentum, Sec. 3.3;
@@ -56,7 +58,7 @@ constexpr int MAXF = 4;
 constexpr int MAXQ = 2 * MAXF + 3;
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
-enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2 };
+enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2, WENO_TENO = 3 };
 
 }  // namespace
 
@@ -70,6 +72,8 @@ typedef struct {
     double gamma[MAXF], pi_inf[MAXF];
     int32_t weno;
     double eps;
+    double teno_ct;   /* TENO threshold C_T (weno = 3) */
+    int32_t model;    /* 0: K = 0 (Allaire); 1: Kapila K div u, two fluids */
 } oc_problem;
 }
 
@@ -160,11 +164,14 @@ struct Lay {
  * Pi    = sum_i alpha_i h_i,  h_i = gamma_i pi_i/(gamma_i - 1). */
 struct Eos {
     int nf;
-    double g[MAXF], h[MAXF];
-    explicit Eos(const oc_problem& P) : nf(P.nf) {
+    int model;
+    double g[MAXF], h[MAXF], gam[MAXF], pinf[MAXF];
+    explicit Eos(const oc_problem& P) : nf(P.nf), model(P.model) {
         for (int i = 0; i < nf; ++i) {
             g[i] = 1.0 / (P.gamma[i] - 1.0);
             h[i] = P.gamma[i] * P.pi_inf[i] / (P.gamma[i] - 1.0);
+            gam[i] = P.gamma[i];
+            pinf[i] = P.pi_inf[i];
         }
     }
     /* Gamma and Pi from the N_f - 1 stored volume fractions; the last one is
@@ -231,14 +238,50 @@ template <class T> T sound_speed(T rho, T p, T Gamma, T Pi) {
     return sqrt(c2);
 }
 
+/* Kapila model, two fluids (Sec. 2.1.1).  With the phasic sound speeds
+ * c_i^2 = gamma_i (p + pi_i)/rho_i, rho_i c_i^2 = Z_i = gamma_i (p + pi_i)
+ * needs no phasic density.
+ *   K = (Z_2 - Z_1) / (Z_1/alpha_1 + Z_2/alpha_2)
+ * (reading: the paper prints Z_2 + Z_1 in the numerator; K must vanish for
+ * identical fluids, and the Kapila model has the difference), and the Wood
+ * mixture sound speed, 1/(rho c^2) = alpha_1/Z_1 + alpha_2/Z_2 (reading:
+ * the sound speed the Kapila model's characteristics carry, used for the
+ * HLLC wave speeds and the CFL step of that model). */
+template <class T> T kapila_K(const Eos& eos, T p, T a1) {
+    T Z1 = T(eos.gam[0]) * (p + T(eos.pinf[0]));
+    T Z2 = T(eos.gam[1]) * (p + T(eos.pinf[1]));
+    T a2 = T(1.0) - a1;
+    return (Z2 - Z1) / (Z1 / a1 + Z2 / a2);
+}
+
+template <class T> T wood_c2(const Eos& eos, T rho, T p, T a1) {
+    T Z1 = T(eos.gam[0]) * (p + T(eos.pinf[0]));
+    T Z2 = T(eos.gam[1]) * (p + T(eos.pinf[1]));
+    T a2 = T(1.0) - a1;
+    return T(1.0) / (rho * (a1 / Z1 + a2 / Z2));
+}
+
+/* Sound speed of the model: the mixture stiffened gas (K = 0) or Wood's
+ * (Kapila). */
+template <class T> T model_sound_speed(const Lay& L, const Eos& eos, const T* w, T rho, T Gamma, T Pi) {
+    if (eos.model == 0) return sound_speed(rho, w[L.E()], Gamma, Pi);
+    T c2 = wood_c2(eos, rho, w[L.E()], w[L.alpha(0)]);
+    if (!(val(c2) > 0.0)) g_bad++;
+    return sqrt(c2);
+}
+
 /* A primitive state is a physical mixture when rho > 0, Gamma > 0 and
- * (Gamma + 1) p + Pi > 0 (so that c^2 > 0). */
+ * (Gamma + 1) p + Pi > 0 (so that c^2 > 0); for the Kapila model also
+ * Z_i = gamma_i (p + pi_i) > 0 for both fluids (the Wood c^2 and K). */
 template <class T> bool physical_state(const Lay& L, const Eos& eos, const T* w) {
     T rho = w[L.rho(0)];
     for (int i = 1; i < L.nf; ++i) rho = rho + w[L.rho(i)];
     T Gamma, Pi;
     eos.mix(w + L.alpha(0), Gamma, Pi);
-    return val(rho) > 0.0 && val(Gamma) > 0.0 && val((Gamma + T(1.0)) * w[L.E()] + Pi) > 0.0;
+    bool ok = val(rho) > 0.0 && val(Gamma) > 0.0 && val((Gamma + T(1.0)) * w[L.E()] + Pi) > 0.0;
+    if (eos.model == 1)
+        ok = ok && val(w[L.E()]) + eos.pinf[0] > 0.0 && val(w[L.E()]) + eos.pinf[1] > 0.0;
+    return ok;
 }
 
 /* ------------------------------------------------------------------ */
@@ -256,7 +299,13 @@ template <class T> bool physical_state(const Lay& L, const Eos& eos, const T* w)
  * mapped (Henrick 2005, cited in Sec. 3.2.1), the JS weights pushed through
  * g_r(w) = w (d_r + d_r^2 - 3 d_r w + w^2)/(d_r^2 + w (1 - 2 d_r)) and
  * renormalised; Z (Sec. 4.2.2, q = 1), alpha_r = d_r (1 + tau/(beta_r + eps)),
- * tau = |beta_0 - beta_2|.  dbg (optional) receives p[3], beta[3], omega[3]. */
+ * tau = |beta_0 - beta_2|.  TENO (Sec. 4.2.2, K = 5: the same three
+ * candidate stencils): gamma_r = d_r (1 + tau/(beta_r + eps))^6,
+ * chi_r = gamma_r / sum gamma, delta_r = 0 if chi_r < C_T else 1,
+ * omega_r = d_r delta_r / sum d delta.  Reading: chi is evaluated with
+ * A_r = 1 + tau/(beta_r + eps) divided by the largest A (a factor common
+ * to numerator and denominator), so that A^6 cannot overflow.
+ * dbg (optional) receives p[3], beta[3], omega[3]. */
 /* Jiang-Shu smoothness indicators of the three candidate stencils
  * (Sec. 4.2.2 with k = 3 on a uniform grid); shared by both edges. */
 template <class T> void weno5_beta(const T* f, T* beta) {
@@ -267,7 +316,7 @@ template <class T> void weno5_beta(const T* f, T* beta) {
 }
 
 template <class T>
-T weno5_edge(const T* f, bool right_edge, int variant, double eps, T* dbg = nullptr) {
+T weno5_edge(const T* f, bool right_edge, int variant, double eps, double ct, T* dbg = nullptr) {
     T p[3], beta[3], d[3];
     if (right_edge) {
         p[0] = (T(2.0) * f[0] - T(7.0) * f[1] + T(11.0) * f[2]) / T(6.0);
@@ -286,6 +335,22 @@ T weno5_edge(const T* f, bool right_edge, int variant, double eps, T* dbg = null
     if (variant == WENO_Z) {
         T tau = fabs(beta[0] - beta[2]);
         for (int r = 0; r < 3; ++r) a[r] = d[r] * (T(1.0) + tau / (beta[r] + T(eps)));
+    } else if (variant == WENO_TENO) {
+        T tau = fabs(beta[0] - beta[2]);
+        T A[3];
+        for (int r = 0; r < 3; ++r) A[r] = T(1.0) + tau / (beta[r] + T(eps));
+        T Am = tmax(tmax(A[0], A[1]), A[2]);
+        T g[3];
+        for (int r = 0; r < 3; ++r) {
+            T x = A[r] / Am;
+            T x2 = x * x;
+            g[r] = d[r] * (x2 * x2 * x2);
+        }
+        T sg = g[0] + g[1] + g[2];
+        for (int r = 0; r < 3; ++r) {
+            T chi = g[r] / sg;
+            a[r] = (chi < T(ct)) ? T(0.0) : d[r];
+        }
     } else {
         for (int r = 0; r < 3; ++r) a[r] = d[r] / sq(T(eps) + beta[r]);
     }
@@ -339,7 +404,7 @@ void hllc(const Lay& L, const Eos& eos, int d, const T* WL, const T* WR, T* F, T
         un[K] = w[L.mom(d)];
         p[K] = w[L.E()];
         E[K] = Gamma * p[K] + Pi + T(0.5) * r * u2;
-        c[K] = sound_speed(r, p[K], Gamma, Pi);
+        c[K] = model_sound_speed(L, eos, w, r, Gamma, Pi);
     }
     T SL = tmin(un[0] - c[0], un[1] - c[1]);
     T SR = tmax(un[0] + c[0], un[1] + c[1]);
@@ -469,9 +534,9 @@ void face_flux(const View& V, const Lay& L, const Eos& eos, int ax, const int* c
     T WL[MAXQ], WR[MAXQ], f[5];
     for (int k = 0; k < L.nq(); ++k) {
         for (int m = 0; m < 5; ++m) f[m] = W[m][k];
-        WL[k] = weno5_edge(f, true, P.weno, P.eps);
+        WL[k] = weno5_edge(f, true, P.weno, P.eps, P.teno_ct);
         for (int m = 0; m < 5; ++m) f[m] = W[m + 1][k];
-        WR[k] = weno5_edge(f, false, P.weno, P.eps);
+        WR[k] = weno5_edge(f, false, P.weno, P.eps, P.teno_ct);
     }
     /* Positivity reading (the paper is silent): if either reconstructed
      * state is not a physical mixture, the face falls back to first-order
@@ -489,14 +554,29 @@ inline double dx_of(const oc_problem& P, int ax) { return (P.hi[ax] - P.lo[ax]) 
 
 /* Contribution of direction ax to the right-hand side of cell c, Eq. (rhs):
  * (F_{c-1/2} - F_{c+1/2})/dx, plus alpha_c (u_{c+1/2} - u_{c-1/2})/dx for the
- * volume-fraction rows (the -h(q) div u term with h = (0,..,0,-alpha)). */
+ * volume-fraction rows (the -h(q) div u term with h = (0,..,0,-alpha)); the
+ * Kapila model adds K_c (u_{c+1/2} - u_{c-1/2})/dx to the alpha_1 row
+ * (alpha_1_t + u . grad alpha_1 = K div u, Sec. 2.1.1), K_c from the cell's
+ * own pressure and volume fraction (Kc = 0 for K = 0). */
 template <class T>
-void cell_term(const Lay& L, double dx, const T* Fm, T um, const T* Fp, T up, const T* qc, T* t) {
+void cell_term(const Lay& L, double dx, const T* Fm, T um, const T* Fp, T up, const T* qc, T Kc, bool kapila,
+               T* t) {
     for (int k = 0; k < L.nq(); ++k) t[k] = (Fm[k] - Fp[k]) / T(dx);
     for (int j = 0; j < L.nf - 1; ++j) {
         int k = L.alpha(j);
-        t[k] = t[k] + qc[k] * (up - um) / T(dx);
+        if (kapila)
+            t[k] = t[k] + (qc[k] + Kc) * (up - um) / T(dx);
+        else
+            t[k] = t[k] + qc[k] * (up - um) / T(dx);
     }
+}
+
+/* K of cell state qc (conservative) for the Kapila model. */
+template <class T> T cell_K(const Lay& L, const Eos& eos, const T* qc) {
+    if (eos.model == 0) return T(0.0);
+    T w[MAXQ];
+    cons_to_prim(L, eos, qc, w);
+    return kapila_K(eos, w[L.E()], w[L.alpha(0)]);
 }
 
 /* Right-hand side L(q) on every interior cell. */
@@ -529,7 +609,8 @@ void rhs_full(const oc_problem& P, const T* q, T* Lout) {
                     int64_t cl = lin(P, c[0], c[1], c[2]);
                     T qc[MAXQ], t[MAXQ];
                     V.load(cl, qc);
-                    cell_term(L, dx, F[s].data(), uf[s], F[s + 1].data(), uf[s + 1], qc, t);
+                    T Kc = cell_K(L, eos, qc);
+                    cell_term(L, dx, F[s].data(), uf[s], F[s + 1].data(), uf[s + 1], qc, Kc, eos.model == 1, t);
                     for (int k = 0; k < nq; ++k) Lout[k * ncell + cl] = Lout[k * ncell + cl] + t[k];
                 }
             }
@@ -545,13 +626,14 @@ void rhs_cell(const View& V, const Lay& L, const Eos& eos, const int* c, T* Lc) 
     for (int k = 0; k < L.nq(); ++k) Lc[k] = T(0.0);
     T qc[MAXQ];
     fetch<T>(V, L, c[0], c[1], c[2], qc);
+    T Kc = cell_K(L, eos, qc);
     for (int ax = 0; ax < P.ndim; ++ax) {
         T Fm[MAXQ], Fp[MAXQ], um, up, t[MAXQ];
         int cm[3] = {c[0], c[1], c[2]};
         cm[ax] -= 1;
         face_flux(V, L, eos, ax, cm, Fm, um);
         face_flux(V, L, eos, ax, c, Fp, up);
-        cell_term(L, dx_of(P, ax), Fm, um, Fp, up, qc, t);
+        cell_term(L, dx_of(P, ax), Fm, um, Fp, up, qc, Kc, eos.model == 1, t);
         for (int k = 0; k < L.nq(); ++k) Lc[k] = Lc[k] + t[k];
     }
 }
@@ -600,7 +682,7 @@ template <class T> double cfl_dt(const oc_problem& P, const T* q, double cfl) {
         for (int i = 1; i < L.nf; ++i) rho = rho + qc[L.rho(i)];
         T Gamma, Pi;
         eos.mix(qc + L.alpha(0), Gamma, Pi);
-        T cs = sound_speed(rho, w[L.E()], Gamma, Pi);
+        T cs = model_sound_speed(L, eos, w, rho, Gamma, Pi);
         for (int ax = 0; ax < P.ndim; ++ax) {
             T s = T(dx_of(P, ax)) / (fabs(w[L.mom(ax)]) + cs);
             m = std::min(m, val(s));
@@ -629,7 +711,9 @@ int check_problem(const oc_problem* P) {
     }
     for (int i = 0; i < P->nf; ++i)
         if (!(P->gamma[i] > 1.0) || !(P->pi_inf[i] >= 0.0)) return -1;
-    if (P->weno < 0 || P->weno > 2 || !(P->eps > 0.0)) return -1;
+    if (P->weno < 0 || P->weno > 3 || !(P->eps > 0.0)) return -1;
+    if (P->weno == WENO_TENO && !(P->teno_ct > 0.0 && P->teno_ct < 1.0)) return -1;
+    if (P->model < 0 || P->model > 1 || (P->model == 1 && P->nf != 2)) return -1;
     return 0;
 }
 
@@ -854,12 +938,12 @@ int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int
     cons_to_prim(L, eos, b, wb);
     g_ops = {0, 0, 0, 0, 0};
     Cnt f[5] = {wa[0], wb[0], wa[0], wb[0], wa[0]};
-    weno5_edge(f, true, P->weno, P->eps);
+    weno5_edge(f, true, P->weno, P->eps, P->teno_ct);
     take(1);
     hllc(L, eos, 0, wa, wb, F, uf);
     take(2);
     Cnt t[MAXQ];
-    cell_term(L, 1.0, F, uf, F, uf, a, t);
+    cell_term(L, 1.0, F, uf, F, uf, a, Cnt(0.0), false, t);
     take(3);
     for (int k = 0; k < nq; ++k) t[k] = Cnt(RK_A2) * a[k] + Cnt(RK_B2) * (b[k] + Cnt(1e-3) * F[k]);
     take(4);
@@ -888,11 +972,11 @@ int oc_block_counts(const oc_problem* P, const double* qa, const double* qb, int
  * out[0..2] candidate values at the right edge, [3..5] beta, [6..8] weights,
  * [9] right-edge value; [10..12] candidates at the left edge, [13..15]
  * weights, [16] left-edge value. */
-void oc_weno5_detail(int variant, double eps, const double* f, double* out) {
+void oc_weno5_detail(int variant, double eps, double ct, const double* f, double* out) {
     double dbg[9];
-    out[9] = weno5_edge(f, true, variant, eps, dbg);
+    out[9] = weno5_edge(f, true, variant, eps, ct, dbg);
     for (int i = 0; i < 9; ++i) out[i] = dbg[i];
-    out[16] = weno5_edge(f, false, variant, eps, dbg);
+    out[16] = weno5_edge(f, false, variant, eps, ct, dbg);
     for (int i = 0; i < 3; ++i) { out[10 + i] = dbg[i]; out[13 + i] = dbg[6 + i]; }
 }
 

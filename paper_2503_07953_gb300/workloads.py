@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 PERIODIC, TRANSMISSIVE, REFLECTIVE = 0, 1, 2
-WENO_JS, WENO_M, WENO_Z = 0, 1, 2
+WENO_JS, WENO_M, WENO_Z, WENO_TENO = 0, 1, 2, 3
 
 
 @dataclass
@@ -41,6 +41,8 @@ class Case:
     steps: int
     weno: int = WENO_M
     eps: float = 1e-40
+    teno_ct: float = 1e-6     # TENO threshold C_T (weno = 3)
+    model: int = 0            # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
 
     @property
     def ndim(self) -> int:
@@ -82,7 +84,8 @@ def reduced_units(case: Case, W: np.ndarray, rho0: float, p0: float) -> tuple:
     W[nf:nf + nd] /= u0
     W[nf + nd] /= p0
     out = Case(case.name, list(case.n), list(case.lo), list(case.hi), list(case.bc_lo), list(case.bc_hi),
-               list(case.gamma), [x / p0 for x in case.pi_inf], case.cfl, case.steps, case.weno, case.eps)
+               list(case.gamma), [x / p0 for x in case.pi_inf], case.cfl, case.steps, case.weno, case.eps,
+               case.teno_ct, case.model)
     return out, W
 
 

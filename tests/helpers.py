@@ -6,7 +6,8 @@ import torch
 
 def oracle_problem(oracle, case):
     return oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
-                          bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
+                          bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps,
+                          teno_ct=case.teno_ct, model=case.model)
 
 
 def solver_for(mfc, case, **kw):

@@ -9,9 +9,9 @@ from paper_2503_07953_gb300 import workloads as wl
 GX, GW = np.polynomial.legendre.leggauss(5)
 
 
-def problem(oracle_lib, case):
+def problem(oracle_lib, case, weno=1):
     return oracle_lib.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
-                              bc_lo=case.bc_lo, bc_hi=case.bc_hi)
+                              bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=weno)
 
 
 def steps_for(h, t_end, speed, base_h):
@@ -20,14 +20,15 @@ def steps_for(h, t_end, speed, base_h):
     return int(math.ceil(t_end / dt))
 
 
-def test_two_component_advection_1d_fifth_order(oracle_lib):
+@pytest.mark.parametrize("weno", [1, 3])
+def test_two_component_advection_1d_fifth_order(oracle_lib, weno):
     """The paper's 1D two-component advection (Sec. 3.5): one period at
     p = u = 1 on the periodic unit interval; RMS error of alpha_1 converges at
-    fifth order with WENO5-M and HLLC."""
+    fifth order with WENO5-M and with TENO5 (Sec. 4.2.2), with HLLC."""
     errs = []
     for n in (16, 32, 64, 128):
         case, W0 = wl.two_component_advection_avg(n)
-        P = problem(oracle_lib, case)
+        P = problem(oracle_lib, case, weno)
         q0 = oracle_lib.prim_to_cons(P, W0)
         nsteps = steps_for(1.0 / n, 1.0, 2.3, 1.0 / 16)
         q, _ = oracle_lib.rk3_run(P, q0, nsteps, dts=np.full(nsteps, 1.0 / nsteps))
