@@ -53,7 +53,7 @@ class _Problem(ctypes.Structure):
         ("bc_lo", ctypes.c_int32 * 3), ("bc_hi", ctypes.c_int32 * 3),
         ("gamma", ctypes.c_double * MAXF), ("pi_inf", ctypes.c_double * MAXF),
         ("weno", ctypes.c_int32), ("eps", ctypes.c_double), ("teno_ct", ctypes.c_double),
-        ("model", ctypes.c_int32),
+        ("model", ctypes.c_int32), ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32),
     ]
 
 
@@ -104,6 +104,8 @@ class Problem:
     eps: float = 1e-40
     teno_ct: float = 1e-6
     model: int = 0                        # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
+    riemann: int = 0                      # 0: HLLC; 1: HLL
+    low_mach: int = 0                     # 0: none; 1: Thornber; 2: anti-dissipation pressure correction
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -141,7 +143,7 @@ class Problem:
             p.gamma[i] = float(self.gamma[i]) if i < self.nf else 0.0
             p.pi_inf[i] = float(self.pi_inf[i]) if i < self.nf else 0.0
         p.weno, p.eps, p.teno_ct = int(self.weno), float(self.eps), float(self.teno_ct)
-        p.model = int(self.model)
+        p.model, p.riemann, p.low_mach = int(self.model), int(self.riemann), int(self.low_mach)
         return p
 
     def dx(self, axis: int) -> float:

@@ -27,7 +27,9 @@
  *   * WENO5 reconstruction of the primitive variables with JS, mapped
  *     (Henrick) and Z weights, Sec. 3.2.1 and Sec. 4.2.2, and the
  *     fifth-order TENO stencil selection of Sec. 4.2.2;
- *   * HLLC approximate Riemann solver, Sec. 3.2.2 (Toro's star states);
+ *   * HLLC and HLL approximate Riemann solvers, Sec. 3.2.2 (Toro), with the
+ *     low-Mach corrections of Sec. 4.2.4 (Thornber's velocity modification,
+ *     Chen's anti-dissipation pressure correction for HLLC);
  *   * ghost cells by periodic wrap, zeroth-order extrapolation or mirror
  *     with negated normal momentum, Sec. 3.3;
  *   * third-order TVD Runge-Kutta, Sec. 3.4 (the same tableau as the
@@ -74,6 +76,8 @@ typedef struct {
     double eps;
     double teno_ct;   /* TENO threshold C_T (weno = 3) */
     int32_t model;    /* 0: K = 0 (Allaire); 1: Kapila K div u, two fluids */
+    int32_t riemann;  /* 0: HLLC; 1: HLL */
+    int32_t low_mach; /* 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC) */
 } oc_problem;
 }
 
@@ -164,9 +168,9 @@ struct Lay {
  * Pi    = sum_i alpha_i h_i,  h_i = gamma_i pi_i/(gamma_i - 1). */
 struct Eos {
     int nf;
-    int model;
+    int model, riemann, low_mach;
     double g[MAXF], h[MAXF], gam[MAXF], pinf[MAXF];
-    explicit Eos(const oc_problem& P) : nf(P.nf), model(P.model) {
+    explicit Eos(const oc_problem& P) : nf(P.nf), model(P.model), riemann(P.riemann), low_mach(P.low_mach) {
         for (int i = 0; i < nf; ++i) {
             g[i] = 1.0 / (P.gamma[i] - 1.0);
             h[i] = P.gamma[i] * P.pi_inf[i] / (P.gamma[i] - 1.0);
@@ -389,7 +393,35 @@ T weno5_edge(const T* f, bool right_edge, int variant, double eps, double ct, T*
  * F receives N_q entries (the alpha slots hold alpha_f u_f); uf the face
  * velocity. */
 template <class T>
-void hllc(const Lay& L, const Eos& eos, int d, const T* WL, const T* WR, T* F, T& uf) {
+void hllc(const Lay& L, const Eos& eos, int d, const T* WL0, const T* WR0, T* F, T& uf) {
+    /* Thornber's low-Mach correction (Sec. 4.2.4): the normal velocities of
+     * the two states are pulled towards their mean by z = min(max(|u_L|/c_L,
+     * |u_R|/c_R), 1) before the solve; reading: the modified states replace
+     * the reconstructed ones everywhere in the solver (wave speeds, fluxes,
+     * star states, total energies). */
+    T WLm[MAXQ], WRm[MAXQ];
+    for (int k = 0; k < L.nq(); ++k) { WLm[k] = WL0[k]; WRm[k] = WR0[k]; }
+    T zlm = T(1.0);
+    if (eos.low_mach != 0) {
+        T cs[2];
+        const T* W0[2] = {WL0, WR0};
+        for (int K = 0; K < 2; ++K) {
+            T r = W0[K][L.rho(0)];
+            for (int i = 1; i < L.nf; ++i) r = r + W0[K][L.rho(i)];
+            T Gamma, Pi;
+            eos.mix(W0[K] + L.alpha(0), Gamma, Pi);
+            cs[K] = model_sound_speed(L, eos, W0[K], r, Gamma, Pi);
+        }
+        T uL = WL0[L.mom(d)], uR = WR0[L.mom(d)];
+        zlm = tmin(tmax(fabs(uL) / cs[0], fabs(uR) / cs[1]), T(1.0));
+        if (eos.low_mach == 1) {
+            T mean = (uL + uR) / T(2.0);
+            WLm[L.mom(d)] = mean + zlm * (uL - uR) / T(2.0);
+            WRm[L.mom(d)] = mean + zlm * (uR - uL) / T(2.0);
+        }
+    }
+    const T* WL = WLm;
+    const T* WR = WRm;
     const T* W[2] = {WL, WR};
     T rho[2], un[2], p[2], E[2], c[2];
     for (int K = 0; K < 2; ++K) {
@@ -408,6 +440,42 @@ void hllc(const Lay& L, const Eos& eos, int d, const T* WL, const T* WR, T* F, T
     }
     T SL = tmin(un[0] - c[0], un[1] - c[1]);
     T SR = tmax(un[0] + c[0], un[1] + c[1]);
+    if (eos.riemann == 1) {
+        /* HLL (Sec. 3.2.2): one averaged state between S_L and S_R,
+         * F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) for every
+         * conserved component, the alpha slots with U = alpha, F = alpha u.
+         * Reading: the face velocity of the alpha div u term is the same
+         * average of u, (S_R u_L - S_L u_R)/(S_R - S_L), so that a uniform
+         * alpha stays uniform. */
+        T FK[2][MAXQ], UK[2][MAXQ];
+        for (int K = 0; K < 2; ++K) {
+            const T* w = W[K];
+            for (int i = 0; i < L.nf; ++i) { FK[K][L.rho(i)] = w[L.rho(i)] * un[K]; UK[K][L.rho(i)] = w[L.rho(i)]; }
+            for (int e = 0; e < L.nd; ++e) {
+                FK[K][L.mom(e)] = rho[K] * un[K] * w[L.mom(e)];
+                if (e == d) FK[K][L.mom(e)] = FK[K][L.mom(e)] + p[K];
+                UK[K][L.mom(e)] = rho[K] * w[L.mom(e)];
+            }
+            FK[K][L.E()] = (E[K] + p[K]) * un[K];
+            UK[K][L.E()] = E[K];
+            for (int j = 0; j < L.nf - 1; ++j) {
+                FK[K][L.alpha(j)] = w[L.alpha(j)] * un[K];
+                UK[K][L.alpha(j)] = w[L.alpha(j)];
+            }
+        }
+        if (SL >= T(0.0)) {
+            for (int k = 0; k < L.nq(); ++k) F[k] = FK[0][k];
+            uf = un[0];
+        } else if (SR <= T(0.0)) {
+            for (int k = 0; k < L.nq(); ++k) F[k] = FK[1][k];
+            uf = un[1];
+        } else {
+            for (int k = 0; k < L.nq(); ++k)
+                F[k] = (SR * FK[0][k] - SL * FK[1][k] + SL * SR * (UK[1][k] - UK[0][k])) / (SR - SL);
+            uf = (SR * un[0] - SL * un[1]) / (SR - SL);
+        }
+        return;
+    }
     T Ss = (p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1])) /
            (rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
 
@@ -439,6 +507,17 @@ void hllc(const Lay& L, const Eos& eos, int d, const T* WL, const T* WR, T* F, T
         }
         T Es = chi * rho[K] * (E[K] / rho[K] + (Ss - un[K]) * (Ss + p[K] / (rho[K] * (SK - un[K]))));
         F[L.E()] = F[L.E()] + SK * (Es - E[K]);
+        if (eos.low_mach == 2) {
+            /* anti-dissipation pressure correction (Sec. 4.2.4) inside the fan:
+             * p_d = rho_L rho_R (S_L - u_L)(S_R - u_R)(u_R - u_L) /
+             *       (rho_R (S_R - u_R) - rho_L (S_L - u_L)),
+             * + (z - 1) p_d on the normal momentum, + (z - 1) p_d S* on the energy */
+            T pd = rho[0] * rho[1] * (SL - un[0]) * (SR - un[1]) * (un[1] - un[0]) /
+                   (rho[1] * (SR - un[1]) - rho[0] * (SL - un[0]));
+            T apc = (zlm - T(1.0)) * pd;
+            F[L.mom(d)] = F[L.mom(d)] + apc;
+            F[L.E()] = F[L.E()] + apc * Ss;
+        }
         uf = Ss;
     } else {
         uf = un[K];
@@ -714,6 +793,8 @@ int check_problem(const oc_problem* P) {
     if (P->weno < 0 || P->weno > 3 || !(P->eps > 0.0)) return -1;
     if (P->weno == WENO_TENO && !(P->teno_ct > 0.0 && P->teno_ct < 1.0)) return -1;
     if (P->model < 0 || P->model > 1 || (P->model == 1 && P->nf != 2)) return -1;
+    if (P->riemann < 0 || P->riemann > 1 || P->low_mach < 0 || P->low_mach > 2) return -1;
+    if (P->low_mach == 2 && P->riemann != 0) return -1;
     return 0;
 }
 

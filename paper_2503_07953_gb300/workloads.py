@@ -43,6 +43,8 @@ class Case:
     eps: float = 1e-40
     teno_ct: float = 1e-6     # TENO threshold C_T (weno = 3)
     model: int = 0            # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
+    riemann: int = 0          # 0: HLLC; 1: HLL
+    low_mach: int = 0         # 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC)
 
     @property
     def ndim(self) -> int:
@@ -85,7 +87,7 @@ def reduced_units(case: Case, W: np.ndarray, rho0: float, p0: float) -> tuple:
     W[nf + nd] /= p0
     out = Case(case.name, list(case.n), list(case.lo), list(case.hi), list(case.bc_lo), list(case.bc_hi),
                list(case.gamma), [x / p0 for x in case.pi_inf], case.cfl, case.steps, case.weno, case.eps,
-               case.teno_ct, case.model)
+               case.teno_ct, case.model, case.riemann, case.low_mach)
     return out, W
 
 
@@ -338,6 +340,35 @@ def bubble_collapse_2d(n: int = 1024, steps: int = 500, dims=None) -> tuple:
 # ---------------------------------------------------------------------------
 # Verification problems
 # ---------------------------------------------------------------------------
+
+def gresho_vortex(n: int, mach: float, R: float = 0.2, gamma: float = 1.4) -> tuple:
+    """Gresho vortex (the low-Mach test of Sec. 4.2.4), one ideal gas, on the
+    periodic unit square centred at (0.5, 0.5): u_phi = u_r (r/R, 2 - r/R, 0)
+    on [0, R), [R, 2R), [2R, inf); p = p_r + rho_r u_r^2 ((r/R)^2/2,
+    (r/R)^2/2 + 4 (1 - r/R + ln(r/R)), -2 + 4 ln 2) on the same intervals;
+    rho_r = 1, u_r = 2 pi R M_r and p_r from M_r = u_r / sqrt(gamma (p_r/rho_r
+    + u_r^2/2)).  One turn takes t_r = 2 pi R / u_r = 1/M_r.  Point values at
+    the cell centres."""
+    case = Case("gresho", [n, n], [0.0, 0.0], [1.0, 1.0], [PERIODIC, PERIODIC], [PERIODIC, PERIODIC],
+                [gamma], [0.0], cfl=0.4, steps=0)
+    X, Y, _ = _centres(case)
+    x, y = X - 0.5, Y - 0.5
+    r = np.sqrt(x * x + y * y)
+    s = r / R
+    rho_r = 1.0
+    u_r = 2.0 * math.pi * R * mach
+    p_r = rho_r * (u_r * u_r / (gamma * mach * mach) - 0.5 * u_r * u_r)
+    uphi = u_r * np.where(s < 1.0, s, np.where(s < 2.0, 2.0 - s, 0.0))
+    with np.errstate(divide="ignore"):
+        mid = 0.5 * s * s + 4.0 * (1.0 - s + np.log(np.where(s > 0, s, 1.0)))
+    p = p_r + rho_r * u_r * u_r * np.where(s < 1.0, 0.5 * s * s, np.where(s < 2.0, mid, -2.0 + 4.0 * math.log(2.0)))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ux = np.where(r > 0, -uphi * y / r, 0.0)
+        uy = np.where(r > 0, uphi * x / r, 0.0)
+    shp = case.shape[1:]
+    W = _assemble(case, [np.ones(shp)], [np.full(shp, rho_r)], [ux, uy], p)
+    return case, W
+
 
 def riemann_1d(n: int, left, right, x0: float, gamma, pi_inf, t_end: float = 0.0,
                bc=TRANSMISSIVE, cfl: float = 0.4, alpha_left: float = 1.0 - 1e-6,

@@ -49,9 +49,9 @@ def test_exact_solution_pressure_velocity_continuous_at_contact(name):
     assert p[0] == pytest.approx(p[1], rel=1e-12)
 
 
-def _run_to(oracle_lib, case, W, t_end, cfl):
+def _run_to(oracle_lib, case, W, t_end, cfl, riemann=0):
     P = oracle_lib.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf,
-                           bc_lo=case.bc_lo, bc_hi=case.bc_hi)
+                           bc_lo=case.bc_lo, bc_hi=case.bc_hi, riemann=riemann)
     q = oracle_lib.prim_to_cons(P, W)
     t, bad = 0.0, 0
     while t < t_end * (1 - 1e-14):
@@ -62,12 +62,14 @@ def _run_to(oracle_lib, case, W, t_end, cfl):
     return oracle_lib.cons_to_prim(P, q), bad
 
 
-def test_sod_converges_to_exact_solution(oracle_lib):
+@pytest.mark.parametrize("riemann", [0, 1])
+def test_sod_converges_to_exact_solution(oracle_lib, riemann):
+    """HLLC and HLL (Sec. 3.2.2) both converge to the exact solution."""
     L, R = CASES["sod"]
     errs = []
     for n in (100, 200, 400):
         case, W = wl.riemann_1d(n, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.5, [1.4], [0.0])
-        w, bad = _run_to(oracle_lib, case, W, 0.2, 0.4)
+        w, bad = _run_to(oracle_lib, case, W, 0.2, 0.4, riemann)
         assert bad == 0
         rho, u, p, _ = er.cell_averages(L, R, 0.5, 0.2, n)
         errs.append([np.abs(w[0, 0, 0] - rho).mean(), np.abs(w[1, 0, 0] - u).mean(),
