@@ -325,6 +325,27 @@ def run_ours(args, world, rank, local):
                           "(unit counts and max clock; 1.253 measured by a DFMA microbenchmark)"}
     if not fp64:
         roof["peak_basis"] = "mixed path: FP32 and FP64 pipes both in use"
+    # the HBM roofline the step would have if it were bandwidth-bound:
+    # algorithmic bytes per cell-step (8 N_q doubles) against the measured copy bandwidth
+    hbm_peak, hbm_basis = 6800.0, "fallback (6.8 TB/s)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm_peak, hbm_basis = float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        pass
+    hbm_ach = 8 * case.nq * 8 * ncell / ((ms / args.steps) / 1e3) / 1e9
+    # DRAM traffic of the sweep kernel from an ncu capture of these very
+    # sources (profiles/sweep_traffic.json), scaled by cells; null otherwise
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
+            tr = json.load(fh)
+        if (tr["source_fingerprint"] == build.source_fingerprint() and tr["precision"] == args.precision
+                and tr["workload"] == args.workload):
+            roof["traffic"] = tr["dram_bytes_per_cell_per_launch"] * ncell
+            roof["traffic_basis"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the x, y, z "
+                                     f"sweeps at {tr['captured']}, scaled by cells")
+    except (OSError, KeyError, ValueError):
+        pass
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -335,6 +356,8 @@ def run_ours(args, world, rank, local):
                        "l2": "state 1.0 GB per buffer > 129 MB L2: no flush needed" if ncell >= 2 ** 22
                        else "state smaller than L2", "parallelism": f"replicas x{world}"},
             "gpu_launches": launches_per_step(case.ndim) * args.steps, "clocks": clk, "roofline": roof,
+            "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm_peak, "frac": hbm_ach / hbm_peak,
+                    "bytes_per_cell_step": 8 * case.nq * 8, "peak_basis": hbm_basis},
             "grind_time_ns": (ms / args.steps) * 1e6 / (ncell * case.nq * 3)}
 
     if not args.no_extras and rank == 0:

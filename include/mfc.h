@@ -81,8 +81,12 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   reduction with the MFC_FP64_FAST arithmetic). */
 typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2 } mfc_precision;
 
-/* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2). */
-typedef enum { MFC_WENO_JS = 0, MFC_WENO_M = 1, MFC_WENO_Z = 2 } mfc_weno;
+/* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2),
+ * and fifth-order TENO (Sec. 4.2.2): the same three candidate stencils, each
+ * switched off when its share chi_r = gamma_r / sum gamma of
+ * gamma_r = d_r (1 + tau/(beta_r + eps))^6 is below the threshold C_T, the
+ * others weighted by their ideal weights renormalised. */
+typedef enum { MFC_WENO_JS = 0, MFC_WENO_M = 1, MFC_WENO_Z = 2, MFC_WENO_TENO = 3 } mfc_weno;
 
 /* Uniform Cartesian grid.  n[d] interior cells on [lo[d], hi[d]] for
  * d < ndim (n[d] = 1 for d >= ndim).  ghost >= 0 is the padding of the
@@ -103,11 +107,40 @@ typedef struct {
     double pi_inf[4];
 } mfc_eos;
 
+/* Volume-fraction equation (Sec. 2.1.1): alpha_t + u . grad alpha = K div u.
+ * MFC_MODEL_K0: K = 0 (the model of Allaire et al.); the sound speed is that
+ *   of the mixture stiffened gas, c^2 = ((Gamma + 1) p + Pi)/(Gamma rho).
+ * MFC_MODEL_KAPILA: two fluids; K = (Z_2 - Z_1)/(Z_1/alpha_1 + Z_2/alpha_2)
+ *   with Z_i = gamma_i (p + pi_i) = rho_i c_i^2, evaluated per cell, and the
+ *   Wood sound speed 1/(rho c^2) = alpha_1/Z_1 + alpha_2/Z_2 in the HLLC wave
+ *   speeds and the CFL step.  States with p + pi_i <= 0 for either fluid are
+ *   non-physical (first-order fallback at faces, MFC_ERR_NONPHYSICAL in cells). */
+typedef enum { MFC_MODEL_K0 = 0, MFC_MODEL_KAPILA = 1 } mfc_model;
+
+/* Approximate Riemann solver (Sec. 3.2.2).  HLLC: Toro's three-wave solver;
+ * the face velocity of the alpha div u term is u_L / S* / S* / u_R.  HLL:
+ * one averaged state between S_L and S_R, F = (S_R F_L - S_L F_R + S_L S_R
+ * (U_R - U_L)) / (S_R - S_L), the volume fraction with U = alpha and
+ * F = alpha u, and the face velocity the same average of u. */
+typedef enum { MFC_RIEMANN_HLLC = 0, MFC_RIEMANN_HLL = 1 } mfc_riemann;
+
+/* Low-Mach corrections (Sec. 4.2.4), with z = min(max(|u_L|/c_L, |u_R|/c_R), 1)
+ * on the face-normal velocities.  THORNBER: the two normal velocities are
+ * replaced by (u_L + u_R)/2 +- z (u_L - u_R)/2 before the solve (both solvers).
+ * APC (HLLC only): (z - 1) p_d is added to the normal momentum flux and
+ * (z - 1) p_d S* to the energy flux inside the fan, with
+ * p_d = rho_L rho_R (S_L - u_L)(S_R - u_R)(u_R - u_L) / (rho_R (S_R - u_R) - rho_L (S_L - u_L)). */
+typedef enum { MFC_LOW_MACH_NONE = 0, MFC_LOW_MACH_THORNBER = 1, MFC_LOW_MACH_APC = 2 } mfc_low_mach;
+
 typedef struct {
     int32_t precision;     /* mfc_precision */
     int32_t weno;          /* mfc_weno */
     double weno_eps;       /* > 0: epsilon of the nonlinear weights (1e-40 for M and Z, 1e-6 for JS) */
     double cfl;            /* > 0: Courant number used when a step is asked for dt <= 0 */
+    double teno_ct;        /* TENO threshold C_T in (0, 1) (MFC_WENO_TENO only; 1e-6 is customary) */
+    int32_t model;         /* mfc_model */
+    int32_t riemann;       /* mfc_riemann */
+    int32_t low_mach;      /* mfc_low_mach */
 } mfc_opts;
 
 typedef struct mfc_ctx mfc_ctx;

@@ -49,6 +49,20 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+def source_fingerprint() -> str:
+    """Hash of the kernel sources alone (no flags, no machine): identifies
+    the code an ncu capture was taken on."""
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for name in sorted(os.listdir(d)):
+            p = os.path.join(d, name)
+            if os.path.isfile(p):
+                h.update(name.encode())
+                with open(p, "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile and link; skipped when sources, flags and machine are unchanged."""
     os.makedirs(BUILD, exist_ok=True)

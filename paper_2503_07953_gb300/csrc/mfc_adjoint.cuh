@@ -33,6 +33,19 @@ struct Recip {
     }
 };
 
+// Partial derivatives of the Kapila K(p, alpha_1) (float64): with
+// Z_i = gamma_i (p + pi_i), N = Z_2 - Z_1, D = Z_1/alpha_1 + Z_2/alpha_2,
+// dK/dp = (N' D - N D') / D^2 and dK/dalpha_1 = -N (dD/dalpha_1) / D^2.
+__device__ __forceinline__ void kapila_K_grad(double p, double a1, const Consts& C, double& dKdp, double& dKda) {
+    const double g1 = C.gam[0], g2 = C.gam[1];
+    const double Z1 = g1 * (p + C.pinf[0]), Z2 = g2 * (p + C.pinf[1]);
+    const double a2 = 1.0 - a1;
+    const double N = Z2 - Z1, D = Z1 / a1 + Z2 / a2;
+    const double iD2 = 1.0 / (D * D);
+    dKdp = ((g2 - g1) * D - N * (g1 / a1 + g2 / a2)) * iD2;
+    dKda = -N * (-Z1 / (a1 * a1) + Z2 / (a2 * a2)) * iD2;
+}
+
 // q_bar += (dW/dq)^T W_bar for the conservative state q of one cell.
 template <int NF, int ND, int MODE = MODE_EXACT>
 __device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* wbar, const Consts& C,
@@ -51,7 +64,7 @@ __device__ __forceinline__ void cons_to_prim_adj(const double* q, const double* 
         u2 = u2 + u[d] * u[d];
     }
     double Gamma, Pi;
-    mixture<NF, double>(q + L::A, C, Gamma, Pi);
+    mixture_mode<NF, M, double>(q + L::A, C, Gamma, Pi);
     const Recip<M, double> rg(Gamma);
     const double ke = 0.5 * rho * u2;
     const double p = rg.div(q[L::E] - ke - Pi);
@@ -190,7 +203,7 @@ __device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const 
 // Adjoint of weno5_cell: given the bars of the right-edge value (vrb) and
 // the left-edge value (vlb), add df to fb[0..4].
 template <int MODE, class R>
-__device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R* fb) {
+__device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R ct, R* fb) {
     const R c13 = R(13.0 / 12.0), c14 = R(0.25);
     const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
     const R A1 = f[1] - R(2) * f[2] + f[3], B1 = f[1] - f[3];
@@ -201,6 +214,25 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
     R beta[3], e, scale;
     weno5_scaled_beta(f[0], f[1], f[2], f[3], f[4], eps, beta, e, scale);
     R betab[3] = {R(0), R(0), R(0)};
+    // TENO: the weights are piecewise constant in the indicators (a
+    // stencil is on or off), so only the candidate values carry bars
+    R omT[2][3];
+    if (variant == WENO_TENO) {
+        const R dR[3] = {R(0.1), R(0.6), R(0.3)}, dL[3] = {R(0.3), R(0.6), R(0.1)};
+        if constexpr (MODE == MODE_EXACT) {
+            const R* ds[2] = {dR, dL};
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                R a[3];
+                teno_select_exact(beta, ds[s], e, ct, a);
+                const R sa = a[0] + a[1] + a[2];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) omT[s][r] = a[r] / sa;
+            }
+        } else {
+            teno_weights(beta, e, ct, dR, dL, omT[0], omT[1]);
+        }
+    }
     const R sixth = R(1) / R(6);
     auto by6 = [&](R x) -> R {
         if constexpr (MODE == MODE_EXACT) return x / R(6);
@@ -212,7 +244,12 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
         p[0] = by6(R(2) * f[0] - R(7) * f[1] + R(11) * f[2]);
         p[1] = by6(-f[1] + R(5) * f[2] + R(2) * f[3]);
         p[2] = by6(R(2) * f[2] + R(5) * f[3] - f[4]);
-        weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vrb, pb, betab);
+        if (variant == WENO_TENO) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) pb[r] += omT[0][r] * vrb;
+        } else {
+            weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vrb, pb, betab);
+        }
         fb[0] += (R(2) * pb[0]) * sixth;
         fb[1] += (R(-7) * pb[0] - pb[1]) * sixth;
         fb[2] += (R(11) * pb[0] + R(5) * pb[1] + R(2) * pb[2]) * sixth;
@@ -225,7 +262,12 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
         p[0] = by6(-f[0] + R(5) * f[1] + R(2) * f[2]);
         p[1] = by6(R(2) * f[1] + R(5) * f[2] - f[3]);
         p[2] = by6(R(11) * f[2] - R(7) * f[3] + R(2) * f[4]);
-        weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vlb, pb, betab);
+        if (variant == WENO_TENO) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) pb[r] += omT[1][r] * vlb;
+        } else {
+            weno5_edge_adj<MODE, R>(p, beta, d, variant, e, vlb, pb, betab);
+        }
         fb[0] += (-pb[0]) * sixth;
         fb[1] += (R(5) * pb[0] + R(2) * pb[1]) * sixth;
         fb[2] += (R(2) * pb[0] + R(5) * pb[1] + R(11) * pb[2]) * sixth;
@@ -246,33 +288,72 @@ __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int var
     fb[4] += a2 + b2;
 }
 
-// Adjoint of hllc: given F_bar[NQ] and uf_bar, add to WLb, WRb.
-// Also returns the forward face velocity in uf_out.
+// Adjoint of hllc (and of its HLL and low-Mach variants): given F_bar[NQ]
+// and uf_bar, add to WLb, WRb.  Also returns the forward face velocity in
+// uf_out.
 template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
-__device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts& C, const R* Fb, R ufb, R* WLb,
+__device__ __forceinline__ void hllc_adj(const R* WL0, const R* WR0, const Consts& C, const R* Fb, R ufb, R* WLb,
                                          R* WRb, R& uf_out) {
     using L = Lay<NF, ND>;
     using Q = Arith<MODE>;
     constexpr int NQ = L::NQ;
+    constexpr int UN = L::MOM + DIR;
     // ---- forward recomputation ----
+    // sound speeds (they do not depend on the velocity, so they are the same
+    // before and after the low-Mach modification)
     R rho[2], un[2], p[2], E[2], c[2], G[2], P[2], u2[2], c2[2];
+    const R* W0[2] = {WL0, WR0};
 #pragma unroll
     for (int K = 0; K < 2; ++K) {
-        const R* w = K ? WR : WL;
+        const R* w = W0[K];
         R r = w[0];
 #pragma unroll
         for (int i = 1; i < NF; ++i) r = r + w[i];
+        mixture_mode<NF, MODE, R>(w + L::A, C, G[K], P[K]);
+        rho[K] = r;
+        p[K] = w[L::E];
+        c2[K] = Q::quot((G[K] + R(1)) * p[K] + P[K], G[K] * r);
+        if constexpr (NF == 2) {
+            if (C.model == 1) c2[K] = wood_c2<MODE, R>(r, p[K], w[L::A], C);
+        }
+        c[K] = sqrt(c2[K]);
+    }
+    // low-Mach z = min(max(|u_L|/c_L, |u_R|/c_R), 1) and Thornber's velocities
+    const R u0L = WL0[UN], u0R = WR0[UN];
+    R zlm = R(1);
+    bool zR = false, zclip = true;
+    R aLz = R(0), aRz = R(0);
+    if (C.low_mach != 0) {
+        aLz = Q::quot(fabs(u0L), c[0]);
+        aRz = Q::quot(fabs(u0R), c[1]);
+        zR = aRz > aLz;
+        const R zm = zR ? aRz : aLz;
+        zclip = R(1) < zm;
+        zlm = zclip ? R(1) : zm;
+    }
+    R WLm[NQ], WRm[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        WLm[k] = WL0[k];
+        WRm[k] = WR0[k];
+    }
+    if (C.low_mach == 1) {
+        const R mean = (u0L + u0R) / R(2);
+        WLm[UN] = mean + zlm * (u0L - u0R) / R(2);
+        WRm[UN] = mean + zlm * (u0R - u0L) / R(2);
+    }
+    const R* WL = WLm;
+    const R* WR = WRm;
+    const R* Wm[2] = {WL, WR};
+#pragma unroll
+    for (int K = 0; K < 2; ++K) {
+        const R* w = Wm[K];
         R s2 = R(0);
 #pragma unroll
         for (int e = 0; e < ND; ++e) s2 = s2 + w[L::MOM + e] * w[L::MOM + e];
-        mixture<NF, R>(w + L::A, C, G[K], P[K]);
-        rho[K] = r;
         u2[K] = s2;
-        un[K] = w[L::MOM + DIR];
-        p[K] = w[L::E];
-        E[K] = G[K] * p[K] + P[K] + R(0.5) * r * s2;
-        c2[K] = Q::quot((G[K] + R(1)) * p[K] + P[K], G[K] * r);
-        c[K] = sqrt(c2[K]);
+        un[K] = w[UN];
+        E[K] = G[K] * p[K] + P[K] + R(0.5) * rho[K] * s2;
     }
     const R aL = un[0] - c[0], aR = un[1] - c[1];
     const bool minR = aR < aL;
@@ -280,136 +361,252 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
     const R bL = un[0] + c[0], bR = un[1] + c[1];
     const bool maxR = bR > bL;
     const R SR = maxR ? bR : bL;
-    const R num = p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]);
-    const R den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
-    const R Ss = Q::quot(num, den);
-    const bool left = Ss >= R(0);
-    const int K = left ? 0 : 1;
-    const R* w = left ? WL : WR;
-    const R rK = rho[K], uK = un[K], pK = p[K], EK = E[K];
-    const R SK = left ? SL : SR;
-    const bool star = left ? (SL < R(0)) : (SR > R(0));
-    const R uf = star ? Ss : uK;
-    uf_out = uf;
 
-    // ---- reverse ----
-    R wb[NQ];
+    // per-side bars: density, normal velocity, pressure, total energy, sound
+    // speed, and the primitive slots read directly
+    R rb[2] = {R(0), R(0)}, unb[2] = {R(0), R(0)}, pb[2] = {R(0), R(0)}, Eb[2] = {R(0), R(0)},
+      cb[2] = {R(0), R(0)};
+    R wbs[2][NQ];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) wb[k] = R(0);
-    R rKb = R(0), uKb = R(0), pKb = R(0), EKb = R(0), SKb = R(0), Ssb = R(0);
-    R ufb_t = ufb;
-    // alpha slots: F = alpha_K uf
+    for (int k = 0; k < NQ; ++k) wbs[0][k] = wbs[1][k] = R(0);
+    R SLb = R(0), SRb = R(0), zb = R(0);
+
+    if (C.riemann == 1) {
+        // ---- HLL ----
+        // physical fluxes and states of both sides (U_alpha = alpha, F_alpha = alpha u)
+        R FK[2][NQ], UK[2][NQ];
 #pragma unroll
-    for (int j = 0; j < NF - 1; ++j) {
-        wb[L::A + j] += Fb[L::A + j] * uf;
-        ufb_t += Fb[L::A + j] * w[L::A + j];
-    }
-    if (star) {
-        Ssb += ufb_t;
-        const R A = SK - uK, B = SK - Ss;
-        const R chi = Q::quot(A, B);
-        const Recip<MODE, R> rB(B), rK_(rK);
-        R chib = R(0);
-        // energy
-        const R Z = rK * (SK - uK);
-        const Recip<MODE, R> rZ(Z);
-        const R Y = Ss + rZ.div(pK);
-        const R X = rK_.div(EK) + (Ss - uK) * Y;
-        const R Es = chi * rK * X;
-        SKb += Fb[L::E] * (Es - EK);
-        const R Esb = Fb[L::E] * SK;
-        EKb -= Fb[L::E] * SK;
-        chib += Esb * rK * X;
-        rKb += Esb * chi * X;
-        const R Xb = Esb * chi * rK;
-        EKb += rK_.div(Xb);
-        rKb -= rK_.div2(Xb * EK);
-        Ssb += Xb * Y;
-        uKb -= Xb * Y;
-        const R Yb = Xb * (Ss - uK);
-        Ssb += Yb;
-        pKb += rZ.div(Yb);
-        const R Zb = rZ.div2(-Yb * pK);
-        rKb += Zb * (SK - uK);
-        SKb += Zb * rK;
-        uKb -= Zb * rK;
-        // momentum
+        for (int K = 0; K < 2; ++K) {
+            const R* w = Wm[K];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                FK[K][i] = w[i] * un[K];
+                UK[K][i] = w[i];
+            }
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                FK[K][L::MOM + e] = rho[K] * un[K] * w[L::MOM + e];
+                if (e == DIR) FK[K][L::MOM + e] = FK[K][L::MOM + e] + p[K];
+                UK[K][L::MOM + e] = rho[K] * w[L::MOM + e];
+            }
+            FK[K][L::E] = (E[K] + p[K]) * un[K];
+            UK[K][L::E] = E[K];
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) {
+                FK[K][L::A + j] = w[L::A + j] * un[K];
+                UK[K][L::A + j] = w[L::A + j];
+            }
+        }
+        R FKb[2][NQ], UKb[2][NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) FKb[0][k] = FKb[1][k] = UKb[0][k] = UKb[1][k] = R(0);
+        if (SL >= R(0)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) FKb[0][k] = Fb[k];
+            uf_out = un[0];
+            unb[0] += ufb;
+        } else if (SR <= R(0)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) FKb[1][k] = Fb[k];
+            uf_out = un[1];
+            unb[1] += ufb;
+        } else {
+            const Recip<MODE, R> rW(SR - SL);
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                const R dU = UK[1][k] - UK[0][k];
+                const R Fk = rW.div(SR * FK[0][k] - SL * FK[1][k] + SL * SR * dU);
+                FKb[0][k] = rW.div(Fb[k] * SR);
+                FKb[1][k] = rW.div(-Fb[k] * SL);
+                UKb[1][k] = rW.div(Fb[k] * SL * SR);
+                UKb[0][k] = -UKb[1][k];
+                SRb += rW.div(Fb[k] * (FK[0][k] + SL * dU - Fk));
+                SLb += rW.div(Fb[k] * (-FK[1][k] + SR * dU + Fk));
+            }
+            const R uf = rW.div(SR * un[0] - SL * un[1]);
+            uf_out = uf;
+            unb[0] += rW.div(ufb * SR);
+            unb[1] -= rW.div(ufb * SL);
+            SRb += rW.div(ufb * (un[0] - uf));
+            SLb += rW.div(ufb * (uf - un[1]));
+        }
+        // F_K and U_K back to the side's variables
+#pragma unroll
+        for (int K = 0; K < 2; ++K) {
+            const R* w = Wm[K];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                wbs[K][i] += FKb[K][i] * un[K] + UKb[K][i];
+                unb[K] += FKb[K][i] * w[i];
+            }
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                const R Fe = FKb[K][L::MOM + e], Ue = UKb[K][L::MOM + e];
+                rb[K] += Fe * un[K] * w[L::MOM + e] + Ue * w[L::MOM + e];
+                unb[K] += Fe * rho[K] * w[L::MOM + e];
+                wbs[K][L::MOM + e] += Fe * rho[K] * un[K] + Ue * rho[K];
+                if (e == DIR) pb[K] += Fe;
+            }
+            Eb[K] += FKb[K][L::E] * un[K] + UKb[K][L::E];
+            pb[K] += FKb[K][L::E] * un[K];
+            unb[K] += FKb[K][L::E] * (E[K] + p[K]);
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) {
+                wbs[K][L::A + j] += FKb[K][L::A + j] * un[K] + UKb[K][L::A + j];
+                unb[K] += FKb[K][L::A + j] * w[L::A + j];
+            }
+        }
+    } else {
+        // ---- HLLC ----
+        const R num = p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]);
+        const R den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
+        const R Ss = Q::quot(num, den);
+        const bool left = Ss >= R(0);
+        const int K = left ? 0 : 1;
+        const R* w = left ? WL : WR;
+        const R rK = rho[K], uK = un[K], pK = p[K], EK = E[K];
+        const R SK = left ? SL : SR;
+        const bool star = left ? (SL < R(0)) : (SR > R(0));
+        const R uf = star ? Ss : uK;
+        uf_out = uf;
+
+        R* wb = wbs[K];
+        R rKb = R(0), uKb = R(0), pKb = R(0), EKb = R(0), SKb = R(0), Ssb = R(0);
+        R ufb_t = ufb;
+        // alpha slots: F = alpha_K uf
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) {
+            wb[L::A + j] += Fb[L::A + j] * uf;
+            ufb_t += Fb[L::A + j] * w[L::A + j];
+        }
+        if (star) {
+            Ssb += ufb_t;
+            if (C.low_mach == 2) {
+                // anti-dissipation pressure correction: + (z - 1) p_d on the
+                // normal momentum, + (z - 1) p_d S* on the energy
+                const R A1 = SL - un[0], B1 = SR - un[1], dun = un[1] - un[0];
+                const R Nn = rho[0] * rho[1] * A1 * B1 * dun;
+                const R Dd = rho[1] * B1 - rho[0] * A1;
+                const Recip<MODE, R> rDd(Dd);
+                const R pd = rDd.div(Nn);
+                const R apc = (zlm - R(1)) * pd;
+                const R apcb = Fb[UN] + Fb[L::E] * Ss;
+                Ssb += Fb[L::E] * apc;
+                zb += apcb * pd;
+                const R pdb = apcb * (zlm - R(1));
+                const R Nnb = rDd.div(pdb);
+                const R Ddb = rDd.div(-pdb * pd);
+                rb[0] += Nnb * rho[1] * A1 * B1 * dun - Ddb * A1;
+                rb[1] += Nnb * rho[0] * A1 * B1 * dun + Ddb * B1;
+                const R A1b = Nnb * rho[0] * rho[1] * B1 * dun - Ddb * rho[0];
+                const R B1b = Nnb * rho[0] * rho[1] * A1 * dun + Ddb * rho[1];
+                const R dunb = Nnb * rho[0] * rho[1] * A1 * B1;
+                SLb += A1b;
+                unb[0] -= A1b + dunb;
+                SRb += B1b;
+                unb[1] += dunb - B1b;
+            }
+            const R A = SK - uK, B = SK - Ss;
+            const R chi = Q::quot(A, B);
+            const Recip<MODE, R> rB(B), rK_(rK);
+            R chib = R(0);
+            // energy
+            const R Z = rK * (SK - uK);
+            const Recip<MODE, R> rZ(Z);
+            const R Y = Ss + rZ.div(pK);
+            const R X = rK_.div(EK) + (Ss - uK) * Y;
+            const R Es = chi * rK * X;
+            SKb += Fb[L::E] * (Es - EK);
+            const R Esb = Fb[L::E] * SK;
+            EKb -= Fb[L::E] * SK;
+            chib += Esb * rK * X;
+            rKb += Esb * chi * X;
+            const R Xb = Esb * chi * rK;
+            EKb += rK_.div(Xb);
+            rKb -= rK_.div2(Xb * EK);
+            Ssb += Xb * Y;
+            uKb -= Xb * Y;
+            const R Yb = Xb * (Ss - uK);
+            Ssb += Yb;
+            pKb += rZ.div(Yb);
+            const R Zb = rZ.div2(-Yb * pK);
+            rKb += Zb * (SK - uK);
+            SKb += Zb * rK;
+            uKb -= Zb * rK;
+            // momentum
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                const R Fe = Fb[L::MOM + e];
+                const R we = w[L::MOM + e];
+                const R ve = (e == DIR) ? Ss : we;
+                SKb += Fe * (chi * rK * ve - rK * we);
+                chib += Fe * SK * rK * ve;
+                rKb += Fe * SK * (chi * ve - we);
+                if (e == DIR) {
+                    Ssb += Fe * SK * chi * rK;
+                    wb[L::MOM + e] -= Fe * SK * rK;
+                } else {
+                    wb[L::MOM + e] += Fe * SK * rK * (chi - R(1));
+                }
+            }
+            // partial densities
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                SKb += Fb[i] * (chi - R(1)) * w[i];
+                chib += Fb[i] * SK * w[i];
+                wb[i] += Fb[i] * SK * (chi - R(1));
+            }
+            // chi = A / B
+            const R Ab = rB.div(chib);
+            const R Bb = rB.div(-chib * chi);
+            SKb += Ab + Bb;
+            uKb -= Ab;
+            Ssb -= Bb;
+        } else {
+            uKb += ufb_t;
+        }
+        // physical flux of side K
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {
+            wb[i] += Fb[i] * uK;
+            uKb += Fb[i] * w[i];
+        }
 #pragma unroll
         for (int e = 0; e < ND; ++e) {
             const R Fe = Fb[L::MOM + e];
-            const R we = w[L::MOM + e];
-            const R ve = (e == DIR) ? Ss : we;
-            SKb += Fe * (chi * rK * ve - rK * we);
-            chib += Fe * SK * rK * ve;
-            rKb += Fe * SK * (chi * ve - we);
-            if (e == DIR) {
-                Ssb += Fe * SK * chi * rK;
-                wb[L::MOM + e] -= Fe * SK * rK;
-            } else {
-                wb[L::MOM + e] += Fe * SK * rK * (chi - R(1));
-            }
+            rKb += Fe * uK * w[L::MOM + e];
+            uKb += Fe * rK * w[L::MOM + e];
+            wb[L::MOM + e] += Fe * rK * uK;
+            if (e == DIR) pKb += Fe;
         }
-        // partial densities
-#pragma unroll
-        for (int i = 0; i < NF; ++i) {
-            SKb += Fb[i] * (chi - R(1)) * w[i];
-            chib += Fb[i] * SK * w[i];
-            wb[i] += Fb[i] * SK * (chi - R(1));
-        }
-        // chi = A / B
-        const R Ab = rB.div(chib);
-        const R Bb = rB.div(-chib * chi);
-        SKb += Ab + Bb;
-        uKb -= Ab;
-        Ssb -= Bb;
-    } else {
-        uKb += ufb_t;
-    }
-    // physical flux of side K
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-        wb[i] += Fb[i] * uK;
-        uKb += Fb[i] * w[i];
-    }
-#pragma unroll
-    for (int e = 0; e < ND; ++e) {
-        const R Fe = Fb[L::MOM + e];
-        rKb += Fe * uK * w[L::MOM + e];
-        uKb += Fe * rK * w[L::MOM + e];
-        wb[L::MOM + e] += Fe * rK * uK;
-        if (e == DIR) pKb += Fe;
-    }
-    EKb += Fb[L::E] * uK;
-    pKb += Fb[L::E] * uK;
-    uKb += Fb[L::E] * (EK + pK);
+        EKb += Fb[L::E] * uK;
+        pKb += Fb[L::E] * uK;
+        uKb += Fb[L::E] * (EK + pK);
 
-    // per-side bars
-    R rb[2] = {R(0), R(0)}, unb[2] = {R(0), R(0)}, pb[2] = {R(0), R(0)}, Eb[2] = {R(0), R(0)},
-      cb[2] = {R(0), R(0)};
-    rb[K] += rKb;
-    unb[K] += uKb;
-    pb[K] += pKb;
-    Eb[K] += EKb;
-    R SLb = left ? SKb : R(0);
-    R SRb = left ? R(0) : SKb;
-    // Ss = num / den
-    const Recip<MODE, R> rden(den);
-    const R numb = rden.div(Ssb);
-    const R denb = rden.div(-Ssb * Ss);
-    pb[1] += numb;
-    pb[0] -= numb;
-    rb[0] += numb * un[0] * (SL - un[0]);
-    unb[0] += numb * rho[0] * (SL - R(2) * un[0]);
-    SLb += numb * rho[0] * un[0];
-    rb[1] -= numb * un[1] * (SR - un[1]);
-    unb[1] -= numb * rho[1] * (SR - R(2) * un[1]);
-    SRb -= numb * rho[1] * un[1];
-    rb[0] += denb * (SL - un[0]);
-    SLb += denb * rho[0];
-    unb[0] -= denb * rho[0];
-    rb[1] -= denb * (SR - un[1]);
-    SRb -= denb * rho[1];
-    unb[1] += denb * rho[1];
+        rb[K] += rKb;
+        unb[K] += uKb;
+        pb[K] += pKb;
+        Eb[K] += EKb;
+        if (left) SLb += SKb; else SRb += SKb;
+        // Ss = num / den
+        const Recip<MODE, R> rden(den);
+        const R numb = rden.div(Ssb);
+        const R denb = rden.div(-Ssb * Ss);
+        pb[1] += numb;
+        pb[0] -= numb;
+        rb[0] += numb * un[0] * (SL - un[0]);
+        unb[0] += numb * rho[0] * (SL - R(2) * un[0]);
+        SLb += numb * rho[0] * un[0];
+        rb[1] -= numb * un[1] * (SR - un[1]);
+        unb[1] -= numb * rho[1] * (SR - R(2) * un[1]);
+        SRb -= numb * rho[1] * un[1];
+        rb[0] += denb * (SL - un[0]);
+        SLb += denb * rho[0];
+        unb[0] -= denb * rho[0];
+        rb[1] -= denb * (SR - un[1]);
+        SRb -= denb * rho[1];
+        unb[1] += denb * rho[1];
+    }
     // wave speeds
     if (minR) {
         unb[1] += SLb;
@@ -425,42 +622,94 @@ __device__ __forceinline__ void hllc_adj(const R* WL, const R* WR, const Consts&
         unb[0] += SRb;
         cb[0] += SRb;
     }
-    // merge the side-K primitive bars collected in wb
-    R* outs[2] = {WLb, WRb};
-    {
-        R* o = outs[K];
+
+    // bars of a side's primitive slots from a bar of its sound speed:
+    // c = sqrt(c2), c2 = ((G + 1) p + P) / (G r), or Wood's
+    // c2 = 1 / (r (a1/Z1 + a2/Z2)) for the Kapila model
+    auto c_bar = [&](int S, R cbar, R* o) {
+        const R* ws = W0[S];
+        const R c2b = Recip<MODE, R>(R(2) * c[S]).div(cbar);
+        bool wood = false;
+        if constexpr (NF == 2) {
+            if (C.model == 1) {
+                wood = true;
+                const R g1 = phasic<R>(C.gam, C.gamf, 0), g2 = phasic<R>(C.gam, C.gamf, 1);
+                const R Z1 = g1 * (p[S] + phasic<R>(C.pinf, C.pinff, 0));
+                const R Z2 = g2 * (p[S] + phasic<R>(C.pinf, C.pinff, 1));
+                const R a1 = ws[L::A], a2 = R(1) - a1;
+                const Recip<MODE, R> rZ1(Z1), rZ2(Z2);
+                const R Dw = rZ1.div(a1) + rZ2.div(a2);
+                const R Dwb = Recip<MODE, R>(Dw).div(-c2b * c2[S]);
+                const R rbs = Recip<MODE, R>(rho[S]).div(-c2b * c2[S]);
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) o[k] += wb[k];
-    }
+                for (int i = 0; i < NF; ++i) o[i] += rbs;
+                o[L::E] -= Dwb * (g1 * rZ1.div2(a1) + g2 * rZ2.div2(a2));
+                o[L::A] += Dwb * (rZ1.div(R(1)) - rZ2.div(R(1)));
+            }
+        }
+        if (!wood) {
+            const R Dd = G[S] * rho[S];
+            const Recip<MODE, R> rDd(Dd);
+            const R Nnb = rDd.div(c2b);
+            const R Ddb = rDd.div(-c2b * c2[S]);
+            const R Gb = Nnb * p[S] + Ddb * rho[S];
+            const R Pb = Nnb;
+            o[L::E] += Nnb * (G[S] + R(1));
+            const R rbs = Ddb * G[S];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) o[i] += rbs;
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j)
+                o[L::A + j] += Gb * (coef_g<R>(C, j) - coef_g<R>(C, NF - 1)) +
+                               Pb * (coef_h<R>(C, j) - coef_h<R>(C, NF - 1));
+        }
+    };
+
+    // bars of the (possibly modified) states
+    R Wb[2][NQ];
 #pragma unroll
     for (int S = 0; S < 2; ++S) {
-        const R* ws = S ? WR : WL;
-        R* o = outs[S];
-        // c = sqrt(c2), c2 = ((G + 1) p + P) / (G r)
-        const R c2b = Recip<MODE, R>(R(2) * c[S]).div(cb[S]);
-        const R Dd = G[S] * rho[S];
-        const Recip<MODE, R> rDd(Dd);
-        const R Nnb = rDd.div(c2b);
-        const R Ddb = rDd.div(-c2b * c2[S]);
-        R Gb = Nnb * p[S] + Ddb * rho[S];
-        R Pb = Nnb;
-        R pbs = pb[S] + Nnb * (G[S] + R(1));
-        R rbs = rb[S] + Ddb * G[S];
+        const R* ws = Wm[S];
+        R* o = Wb[S];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) o[k] = wbs[S][k];
+        c_bar(S, cb[S], o);
         // E = G p + P + 0.5 r u2
-        Gb += Eb[S] * p[S];
-        pbs += Eb[S] * G[S];
-        Pb += Eb[S];
-        rbs += Eb[S] * R(0.5) * u2[S];
+        const R Gb = Eb[S] * p[S];
+        const R Pb = Eb[S];
+        o[L::E] += pb[S] + Eb[S] * G[S];
+        const R rbs = rb[S] + Eb[S] * R(0.5) * u2[S];
         const R u2b = Eb[S] * R(0.5) * rho[S];
 #pragma unroll
         for (int e = 0; e < ND; ++e) o[L::MOM + e] += u2b * R(2) * ws[L::MOM + e];
-        o[L::MOM + DIR] += unb[S];
-        o[L::E] += pbs;
+        o[UN] += unb[S];
 #pragma unroll
         for (int i = 0; i < NF; ++i) o[i] += rbs;
 #pragma unroll
         for (int j = 0; j < NF - 1; ++j)
             o[L::A + j] += Gb * (coef_g<R>(C, j) - coef_g<R>(C, NF - 1)) + Pb * (coef_h<R>(C, j) - coef_h<R>(C, NF - 1));
+    }
+    // Thornber: the normal velocities of the modified states back to the
+    // reconstructed ones, and their dependence on z
+    if (C.low_mach == 1) {
+        const R bL_ = Wb[0][UN], bR_ = Wb[1][UN];
+        zb += bL_ * (u0L - u0R) / R(2) + bR_ * (u0R - u0L) / R(2);
+        Wb[0][UN] = bL_ * (R(1) + zlm) / R(2) + bR_ * (R(1) - zlm) / R(2);
+        Wb[1][UN] = bL_ * (R(1) - zlm) / R(2) + bR_ * (R(1) + zlm) / R(2);
+    }
+    // z = min(max(|u_L|/c_L, |u_R|/c_R), 1): the branch taken
+    if (C.low_mach != 0 && !zclip) {
+        const int S = zR ? 1 : 0;
+        const R u0 = S ? u0R : u0L;
+        const R sg = (u0 >= R(0)) ? R(1) : R(-1);
+        const Recip<MODE, R> rc(c[S]);
+        Wb[S][UN] += zb * sg * rc.div(R(1));
+        c_bar(S, -zb * (S ? aRz : aLz) * rc.div(R(1)), Wb[S]);
+    }
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        WLb[k] += Wb[0][k];
+        WRb[k] += Wb[1][k];
     }
 }
 

@@ -145,7 +145,13 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
     }
     if (o->precision != MFC_FP64 && o->precision != MFC_MIXED && o->precision != MFC_FP64_FAST)
         return "unknown precision";
-    if (o->weno < 0 || o->weno > 2) return "unknown WENO variant";
+    if (o->weno < 0 || o->weno > 3) return "unknown WENO variant";
+    if (o->weno == 3 && !(o->teno_ct > 0.0 && o->teno_ct < 1.0)) return "teno_ct must be in (0, 1)";
+    if (o->model < 0 || o->model > 1) return "unknown model";
+    if (o->model == 1 && e->nfluids != 2) return "the Kapila model needs nfluids = 2";
+    if (o->riemann < 0 || o->riemann > 1) return "unknown Riemann solver";
+    if (o->low_mach < 0 || o->low_mach > 2) return "unknown low-Mach correction";
+    if (o->low_mach == 2 && o->riemann != 0) return "the anti-dissipation pressure correction needs HLLC";
     if (!(o->weno_eps > 0.0) || !std::isfinite(o->weno_eps)) return "weno_eps must be > 0";
     if (!(o->cfl > 0.0) || !std::isfinite(o->cfl)) return "cfl must be > 0";
     return "";
@@ -179,9 +185,26 @@ void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Co
         C.gf[i] = (float)C.g[i];
         C.hf[i] = (float)C.h[i];
     }
+    for (int i = 0; i < e->nfluids; ++i) {
+        C.gd[i] = C.g[i] - C.g[e->nfluids - 1];
+        C.hd[i] = C.h[i] - C.h[e->nfluids - 1];
+        C.gdf[i] = (float)C.gd[i];
+        C.hdf[i] = (float)C.hd[i];
+    }
     C.eps = o->weno_eps;
     // float32 WENO rescales eps with the indicators and floors it (mfc_device.cuh)
     C.epsf = (float)o->weno_eps;
+    C.teno_ct = o->weno == 3 ? o->teno_ct : 0.0;
+    C.teno_ctf = (float)C.teno_ct;
+    C.model = o->model;
+    C.riemann = o->riemann;
+    C.low_mach = o->low_mach;
+    for (int i = 0; i < 2; ++i) {
+        C.gam[i] = i < e->nfluids ? e->gamma[i] : 0.0;
+        C.pinf[i] = i < e->nfluids ? e->pi_inf[i] : 0.0;
+        C.gamf[i] = (float)C.gam[i];
+        C.pinff[i] = (float)C.pinf[i];
+    }
     C.cfl = o->cfl;
     total = C.fstride * C.nq;
 }

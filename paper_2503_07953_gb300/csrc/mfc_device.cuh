@@ -39,14 +39,23 @@ struct Consts {
     double dx[3], inv_dx[3];
     double g[MAXF], h[MAXF];  // 1/(gamma_i - 1), gamma_i pi_i/(gamma_i - 1)
     float gf[MAXF], hf[MAXF];
+    double gd[MAXF], hd[MAXF];  // g_i - g_N, h_i - h_N (fast mixture rules)
+    float gdf[MAXF], hdf[MAXF];
     float inv_dxf[3];
     double eps;
     float epsf;
+    double teno_ct;           // TENO threshold C_T
+    float teno_ctf;
+    int model;                // 0: K = 0; 1: Kapila K div u (two fluids)
+    int riemann;              // 0: HLLC; 1: HLL
+    int low_mach;             // 0: none; 1: Thornber; 2: anti-dissipation pressure correction
+    double gam[2], pinf[2];   // phasic gamma_i, pi_i of the two fluids (Kapila)
+    float gamf[2], pinff[2];
     double cfl;
 };
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
-enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2 };
+enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2, WENO_TENO = 3 };
 
 template <int NF, int ND>
 struct Lay {
@@ -91,6 +100,34 @@ template <> struct Arith<MODE_MIXED> {
     static __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
 };
 
+// Phasic constant i of the precision R (float64 / float32 copies).
+template <class R> __device__ __forceinline__ R phasic(const double* d, const float* f, int i);
+template <> __device__ __forceinline__ double phasic<double>(const double* d, const float*, int i) { return d[i]; }
+template <> __device__ __forceinline__ float phasic<float>(const double*, const float* f, int i) { return f[i]; }
+
+// Kapila model, two fluids (Sec. 2.1.1): with Z_i = gamma_i (p + pi_i)
+// (= rho_i c_i^2 of the phasic sound speeds),
+//   K = (Z_2 - Z_1) / (Z_1/alpha_1 + Z_2/alpha_2)
+// and the Wood mixture sound speed 1/(rho c^2) = alpha_1/Z_1 + alpha_2/Z_2,
+// in the order of these formulas (MODE_EXACT) or with fast quotients.
+template <int MODE, class R>
+__device__ __forceinline__ R kapila_K(R p, R a1, const Consts& C) {
+    using A = Arith<MODE>;
+    const R Z1 = phasic<R>(C.gam, C.gamf, 0) * (p + phasic<R>(C.pinf, C.pinff, 0));
+    const R Z2 = phasic<R>(C.gam, C.gamf, 1) * (p + phasic<R>(C.pinf, C.pinff, 1));
+    const R a2 = R(1) - a1;
+    return A::quot(Z2 - Z1, A::quot(Z1, a1) + A::quot(Z2, a2));
+}
+
+template <int MODE, class R>
+__device__ __forceinline__ R wood_c2(R rho, R p, R a1, const Consts& C) {
+    using A = Arith<MODE>;
+    const R Z1 = phasic<R>(C.gam, C.gamf, 0) * (p + phasic<R>(C.pinf, C.pinff, 0));
+    const R Z2 = phasic<R>(C.gam, C.gamf, 1) * (p + phasic<R>(C.pinf, C.pinff, 1));
+    const R a2 = R(1) - a1;
+    return A::quot(R(1), rho * (A::quot(a1, Z1) + A::quot(a2, Z2)));
+}
+
 // Mixture rules (Sec. 2.1.1) with the stiffened-gas EOS (Sec. 2.2):
 // Gamma = sum alpha_i/(gamma_i - 1), Pi = sum alpha_i gamma_i pi_i/(gamma_i - 1),
 // with alpha_N = 1 - sum of the stored N-1 fractions.
@@ -106,6 +143,34 @@ __device__ __forceinline__ void mixture(const R* alpha, const Consts& C, R& Gamm
     for (int j = 0; j < NF - 1; ++j) {
         Gamma = Gamma + alpha[j] * coef_g<R>(C, j);
         Pi = Pi + alpha[j] * coef_h<R>(C, j);
+    }
+}
+
+// The same mixture rules with alpha_N eliminated: Gamma = g_N + sum_j
+// alpha_j (g_j - g_N), Pi likewise, as fused multiply-adds (MODE_MIXED).
+// The float64 modes keep the form above: with stiff fluids Pi ~ 1e9 is
+// cancelled against p ~ 1e5 in the pressure recovery, and a different
+// rounding of Pi shows up in the right-hand side at ~1e-11.
+template <int NF, int MODE, class R>
+__device__ __forceinline__ void mixture_mode(const R* alpha, const Consts& C, R& Gamma, R& Pi) {
+    if constexpr (MODE != MODE_MIXED) {
+        mixture<NF, R>(alpha, C, Gamma, Pi);
+    } else if constexpr (sizeof(R) == 8) {
+        Gamma = C.g[NF - 1];
+        Pi = C.h[NF - 1];
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) {
+            Gamma = fma(alpha[j], C.gd[j], Gamma);
+            Pi = fma(alpha[j], C.hd[j], Pi);
+        }
+    } else {
+        Gamma = C.gf[NF - 1];
+        Pi = C.hf[NF - 1];
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) {
+            Gamma = fmaf(alpha[j], C.gdf[j], Gamma);
+            Pi = fmaf(alpha[j], C.hdf[j], Pi);
+        }
     }
 }
 
@@ -139,7 +204,7 @@ __device__ __forceinline__ void cons_to_prim(const double* q, double* w, const C
 #pragma unroll
     for (int j = 0; j < NF - 1; ++j) w[L::A + j] = q[L::A + j];
     double Gamma, Pi;
-    mixture<NF, double>(q + L::A, C, Gamma, Pi);
+    mixture_mode<NF, MODE, double>(q + L::A, C, Gamma, Pi);
     const double ke = 0.5 * rho * u2;
     w[L::E] = Arith<MODE>::quot(q[L::E] - ke - Pi, Gamma);
 }
@@ -170,19 +235,17 @@ __device__ __forceinline__ void prim_for_recon(const double* q, R* out, const Co
             ke += m * out[L::MOM + d];
         }
         ke *= 0.5f;
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < NF - 1; ++j) s = s + q[L::A + j];
-        double Pi = (1.0 - s) * C.h[NF - 1];
-#pragma unroll
-        for (int j = 0; j < NF - 1; ++j) Pi = Pi + q[L::A + j] * C.h[j];
-        const double num = (q[L::E] - Pi) - double(ke);
-        float Gamma = float(1.0 - s) * C.gf[NF - 1];
+        // Pi = h_N + sum_j alpha_j (h_j - h_N): N_f - 1 fused multiply-adds
+        // in float64; Gamma the same way in float32
+        double Pi = C.h[NF - 1];
+        float Gamma = C.gf[NF - 1];
 #pragma unroll
         for (int j = 0; j < NF - 1; ++j) {
+            Pi = fma(q[L::A + j], C.hd[j], Pi);
             out[L::A + j] = float(q[L::A + j]);
-            Gamma += out[L::A + j] * C.gf[j];
+            Gamma = fmaf(out[L::A + j], C.gdf[j], Gamma);
         }
+        const double num = (q[L::E] - Pi) - double(ke);
         out[L::E] = __fdividef(float(num), Gamma);
     } else {
         double w[Lay<NF, ND>::NQ];
@@ -194,15 +257,21 @@ __device__ __forceinline__ void prim_for_recon(const double* q, R* out, const Co
 
 // A primitive state is a physical mixture when rho > 0, Gamma > 0 and
 // (Gamma + 1) p + Pi > 0 (so that c^2 > 0).
-template <int NF, int ND, class R>
+template <int NF, int ND, class R, int MODE = MODE_EXACT>
 __device__ __forceinline__ bool physical_state(const R* w, const Consts& C) {
     using L = Lay<NF, ND>;
     R rho = w[0];
 #pragma unroll
     for (int i = 1; i < NF; ++i) rho = rho + w[i];
     R Gamma, Pi;
-    mixture<NF, R>(w + L::A, C, Gamma, Pi);
-    return rho > R(0) && Gamma > R(0) && (Gamma + R(1)) * w[L::E] + Pi > R(0);
+    mixture_mode<NF, MODE, R>(w + L::A, C, Gamma, Pi);
+    bool ok = rho > R(0) && Gamma > R(0) && (Gamma + R(1)) * w[L::E] + Pi > R(0);
+    if constexpr (NF == 2) {
+        // Kapila: both phasic impedances gamma_i (p + pi_i) positive
+        if (C.model == 1) ok = ok && w[L::E] + phasic<R>(C.pinf, C.pinff, 0) > R(0) &&
+                               w[L::E] + phasic<R>(C.pinf, C.pinff, 1) > R(0);
+    }
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -243,13 +312,39 @@ __device__ __forceinline__ void weno5_scaled_beta(R f0, R f1, R f2, R f3, R f4, 
 // d_r (1 + tau/(beta_r + eps)) (Z, q = 1, tau = |beta_0 - beta_2|),
 // w = alpha/sum(alpha); mapped (Henrick 2005):
 // g_r(w) = w (d + d^2 - 3 d w + w^2)/(d^2 + w (1 - 2 d)), omega = g/sum(g).
+// TENO stencil selection of one edge (Sec. 4.2.2) in the MODE_EXACT order:
+// gamma_r = d_r A_r^6, A_r = 1 + tau/(beta_r + eps), evaluated with
+// A_r / max A; a stencil whose share chi_r of gamma is below C_T gets
+// a_r = 0, the others a_r = d_r.
+__device__ __forceinline__ void teno_select_exact(const double* beta, const double* d, double eps, double ct,
+                                                  double* a) {
+    const double tau = fabs(beta[0] - beta[2]);
+    double A[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) A[r] = 1.0 + tau / (beta[r] + eps);
+    double Am = (A[1] > A[0]) ? A[1] : A[0];
+    Am = (A[2] > Am) ? A[2] : Am;
+    double g[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double x = A[r] / Am;
+        const double x2 = x * x;
+        g[r] = d[r] * (x2 * x2 * x2);
+    }
+    const double sg = g[0] + g[1] + g[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) a[r] = (g[r] / sg < ct) ? 0.0 : d[r];
+}
+
 __device__ __forceinline__ double weno5_edge_exact(const double* p, const double* beta, const double* d,
-                                                   int variant, double eps) {
+                                                   int variant, double eps, double ct) {
     double a[3], w[3];
     if (variant == WENO_Z) {
         const double tau = fabs(beta[0] - beta[2]);
 #pragma unroll
         for (int r = 0; r < 3; ++r) a[r] = d[r] * (1.0 + tau / (beta[r] + eps));
+    } else if (variant == WENO_TENO) {
+        teno_select_exact(beta, d, eps, ct, a);
     } else {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -302,8 +397,46 @@ __device__ __forceinline__ void weno5_edge_weights(const R* P, const R* d, int v
     om[2] = w2;
 }
 
+// TENO weights of both edges in the MODE_FAST / MODE_MIXED arithmetic:
+// x_r = A_r / max A with A_r = 1 + tau/(b_r + e) (one reciprocal per
+// stencil and one for the maximum), gamma_r = d_r x_r^6 per edge, stencil r
+// off when gamma_r < C_T sum gamma, weights d_r renormalised over the
+// stencils that stay on.
+template <class R>
+__device__ __forceinline__ void teno_weights(const R* b, R e, R ct, const R* dR, const R* dL, R* omR, R* omL) {
+    const R tau = fabs(b[0] - b[2]);
+    R A[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) A[r] = R(1) + tau * rcp<R>(b[r] + e);
+    R Am = (A[1] > A[0]) ? A[1] : A[0];
+    Am = (A[2] > Am) ? A[2] : Am;
+    const R iAm = rcp<R>(Am);
+    R x6[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const R x = A[r] * iAm;
+        const R x2 = x * x;
+        x6[r] = x2 * x2 * x2;
+    }
+    const R* ds[2] = {dR, dL};
+    R* oms[2] = {omR, omL};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const R* d = ds[s];
+        const R g0 = d[0] * x6[0], g1 = d[1] * x6[1], g2 = d[2] * x6[2];
+        const R lim = ct * (g0 + g1 + g2);
+        const R a0 = (g0 < lim) ? R(0) : d[0];
+        const R a1 = (g1 < lim) ? R(0) : d[1];
+        const R a2 = (g2 < lim) ? R(0) : d[2];
+        const R inv = rcp<R>(a0 + a1 + a2);
+        oms[s][0] = a0 * inv;
+        oms[s][1] = a1 * inv;
+        oms[s][2] = a2 * inv;
+    }
+}
+
 template <int MODE, class R>
-__device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int variant, R eps, R& vl, R& vr) {
+__device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int variant, R eps, R ct, R& vl, R& vr) {
     if constexpr (MODE == MODE_EXACT) {
         const double c13 = 13.0 / 12.0, c14 = 0.25;
         double beta[3];
@@ -317,13 +450,13 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
             const double d[3] = {0.1, 0.6, 0.3};
             const double p[3] = {(2.0 * f0 - 7.0 * f1 + 11.0 * f2) / 6.0, (-f1 + 5.0 * f2 + 2.0 * f3) / 6.0,
                                  (2.0 * f2 + 5.0 * f3 - f4) / 6.0};
-            vr = weno5_edge_exact(p, beta, d, variant, eps);
+            vr = weno5_edge_exact(p, beta, d, variant, eps, ct);
         }
         {
             const double d[3] = {0.3, 0.6, 0.1};
             const double p[3] = {(-f0 + 5.0 * f1 + 2.0 * f2) / 6.0, (2.0 * f1 + 5.0 * f2 - f3) / 6.0,
                                  (11.0 * f2 - 7.0 * f3 + 2.0 * f4) / 6.0};
-            vl = weno5_edge_exact(p, beta, d, variant, eps);
+            vl = weno5_edge_exact(p, beta, d, variant, eps, ct);
         }
     } else {
         R b[3], e, scale;
@@ -331,21 +464,25 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
         R P[3];
         const R dR[3] = {R(0.1), R(0.6), R(0.3)}, dL[3] = {R(0.3), R(0.6), R(0.1)};
         R omR[3], omL[3];
-        if (variant == WENO_Z) {
-            const R tau = fabs(b[0] - b[2]);
-            const R t0 = b[0] + e, t1 = b[1] + e, t2 = b[2] + e;
-            P[0] = (t0 + tau) * (t1 * t2);
-            P[1] = (t1 + tau) * (t0 * t2);
-            P[2] = (t2 + tau) * (t0 * t1);
+        if (variant == WENO_TENO) {
+            teno_weights(b, e, ct, dR, dL, omR, omL);
         } else {
-            const R t0 = e + b[0], t1 = e + b[1], t2 = e + b[2];
-            const R s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
-            P[0] = s1 * s2;
-            P[1] = s0 * s2;
-            P[2] = s0 * s1;
+            if (variant == WENO_Z) {
+                const R tau = fabs(b[0] - b[2]);
+                const R t0 = b[0] + e, t1 = b[1] + e, t2 = b[2] + e;
+                P[0] = (t0 + tau) * (t1 * t2);
+                P[1] = (t1 + tau) * (t0 * t2);
+                P[2] = (t2 + tau) * (t0 * t1);
+            } else {
+                const R t0 = e + b[0], t1 = e + b[1], t2 = e + b[2];
+                const R s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
+                P[0] = s1 * s2;
+                P[1] = s0 * s2;
+                P[2] = s0 * s1;
+            }
+            weno5_edge_weights(P, dR, variant, omR);
+            weno5_edge_weights(P, dL, variant, omL);
         }
-        weno5_edge_weights(P, dR, variant, omR);
-        weno5_edge_weights(P, dL, variant, omL);
         const R sixth = R(1.0 / 6.0);
         const R pr0 = (R(2) * f0 - R(7) * f1 + R(11) * f2) * sixth;
         const R pr1 = (-f1 + R(5) * f2 + R(2) * f3) * sixth;
@@ -366,33 +503,111 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
 // the volume-fraction slots receive alpha_K uf.  bad is set when a squared
 // sound speed is not positive.
 template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
-__device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, R* F, R& uf, bool& bad) {
+__device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C, R* F, R& uf, bool& bad) {
     using L = Lay<NF, ND>;
     using A = Arith<MODE>;
-    R rho[2], un[2], p[2], E[2], c[2];
+    constexpr int NQ = L::NQ;
+    constexpr int UN = L::MOM + DIR;
+    // sound speeds of the reconstructed states (independent of the velocity)
+    R rho[2], un[2], p[2], E[2], c[2], Gm[2], Pm[2];
+    const R* W0[2] = {WL0, WR0};
 #pragma unroll
     for (int K = 0; K < 2; ++K) {
-        const R* w = K ? WR : WL;
+        const R* w = W0[K];
         R r = w[0];
 #pragma unroll
         for (int i = 1; i < NF; ++i) r = r + w[i];
+        mixture_mode<NF, MODE, R>(w + L::A, C, Gm[K], Pm[K]);
+        rho[K] = r;
+        p[K] = w[L::E];
+        R c2 = A::quot((Gm[K] + R(1)) * p[K] + Pm[K], Gm[K] * r);
+        if constexpr (NF == 2) {
+            if (C.model == 1) c2 = wood_c2<MODE, R>(r, p[K], w[L::A], C);
+        }
+        bad |= !(c2 > R(0));
+        c[K] = sqrt(c2);
+    }
+    // low-Mach corrections (Sec. 4.2.4): z = min(max(|u_L|/c_L, |u_R|/c_R), 1);
+    // Thornber's modification pulls the normal velocities towards their mean
+    R zlm = R(1);
+    R WLm[NQ], WRm[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        WLm[k] = WL0[k];
+        WRm[k] = WR0[k];
+    }
+    if (C.low_mach != 0) {
+        const R uL = WL0[UN], uR = WR0[UN];
+        const R aLz = A::quot(fabs(uL), c[0]), aRz = A::quot(fabs(uR), c[1]);
+        const R zm = (aRz > aLz) ? aRz : aLz;
+        zlm = (R(1) < zm) ? R(1) : zm;
+        if (C.low_mach == 1) {
+            const R mean = (uL + uR) / R(2);
+            WLm[UN] = mean + zlm * (uL - uR) / R(2);
+            WRm[UN] = mean + zlm * (uR - uL) / R(2);
+        }
+    }
+    const R* WL = WLm;
+    const R* WR = WRm;
+#pragma unroll
+    for (int K = 0; K < 2; ++K) {
+        const R* w = K ? WR : WL;
         R u2 = R(0);
 #pragma unroll
         for (int e = 0; e < ND; ++e) u2 = u2 + w[L::MOM + e] * w[L::MOM + e];
-        R Gamma, Pi;
-        mixture<NF, R>(w + L::A, C, Gamma, Pi);
-        rho[K] = r;
-        un[K] = w[L::MOM + DIR];
-        p[K] = w[L::E];
-        E[K] = Gamma * p[K] + Pi + R(0.5) * r * u2;
-        const R c2 = A::quot((Gamma + R(1)) * p[K] + Pi, Gamma * r);
-        bad |= !(c2 > R(0));
-        c[K] = sqrt(c2);
+        un[K] = w[UN];
+        E[K] = Gm[K] * p[K] + Pm[K] + R(0.5) * rho[K] * u2;
     }
     const R aL = un[0] - c[0], aR = un[1] - c[1];
     const R SL = (aR < aL) ? aR : aL;
     const R bL = un[0] + c[0], bR = un[1] + c[1];
     const R SR = (bR > bL) ? bR : bL;
+
+    if (C.riemann == 1) {
+        // HLL (Sec. 3.2.2): F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)
+        // in the fan for every conserved component (U_alpha = alpha,
+        // F_alpha = alpha u); the face velocity of alpha div u is the same
+        // average of u
+        R FK[2][NQ], UK[2][NQ];
+#pragma unroll
+        for (int K = 0; K < 2; ++K) {
+            const R* w = K ? WR : WL;
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                FK[K][i] = w[i] * un[K];
+                UK[K][i] = w[i];
+            }
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                FK[K][L::MOM + e] = rho[K] * un[K] * w[L::MOM + e];
+                if (e == DIR) FK[K][L::MOM + e] = FK[K][L::MOM + e] + p[K];
+                UK[K][L::MOM + e] = rho[K] * w[L::MOM + e];
+            }
+            FK[K][L::E] = (E[K] + p[K]) * un[K];
+            UK[K][L::E] = E[K];
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) {
+                FK[K][L::A + j] = w[L::A + j] * un[K];
+                UK[K][L::A + j] = w[L::A + j];
+            }
+        }
+        if (SL >= R(0)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) F[k] = FK[0][k];
+            uf = un[0];
+        } else if (SR <= R(0)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) F[k] = FK[1][k];
+            uf = un[1];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k)
+                F[k] = A::quot(SR * FK[0][k] - SL * FK[1][k] + SL * SR * (UK[1][k] - UK[0][k]), SR - SL);
+            uf = A::quot(SR * un[0] - SL * un[1], SR - SL);
+        }
+        return;
+    }
+
     const R Ss = A::quot(p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]),
                          rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
 
@@ -427,6 +642,14 @@ __device__ __forceinline__ void hllc(const R* WL, const R* WR, const Consts& C, 
         }
         const R Es = chi * rK * (A::quot(EK, rK) + (Ss - uK) * (Ss + A::quot(pK, rK * (SK - uK))));
         F[L::E] = F[L::E] + SK * (Es - EK);
+        if (C.low_mach == 2) {
+            // anti-dissipation pressure correction (Sec. 4.2.4)
+            const R pd = A::quot(rho[0] * rho[1] * (SL - un[0]) * (SR - un[1]) * (un[1] - un[0]),
+                                 rho[1] * (SR - un[1]) - rho[0] * (SL - un[0]));
+            const R apc = (zlm - R(1)) * pd;
+            F[UN] = F[UN] + apc;
+            F[L::E] = F[L::E] + apc * Ss;
+        }
         uf = Ss;
     } else {
         uf = uK;

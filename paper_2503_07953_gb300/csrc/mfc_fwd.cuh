@@ -41,6 +41,7 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
     const int bclo = C.bc_lo[DIR], bchi = C.bc_hi[DIR];
     const int variant = C.weno;
     const R eps = sizeof(R) == 8 ? R(C.eps) : R(C.epsf);
+    const R ct = sizeof(R) == 8 ? R(C.teno_ct) : R(C.teno_ctf);
     const R inv_dx = sizeof(R) == 8 ? R(C.inv_dx[DIR]) : R(C.inv_dxf[DIR]);
     const double dx = C.dx[DIR];
     bool bad = false;
@@ -64,14 +65,39 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
     const double dtv = (A.out_kind != 0) ? *A.dt : 0.0;
 
     for (int64_t m = s0 - 1; m <= s1; ++m) {
+        if constexpr (MODE == MODE_MIXED) {
+            // the float32 march is bound by the latency of its loads: bring
+            // the state two cells ahead of the window, and the accumulator and
+            // q^n of the cell finished two iterations later, into L2 now
+            const int64_t cpf = m + 4;
+            if (cpf < n) {
+                const double* pq = A.q + base + cpf * S;
+#pragma unroll
+                for (int f = 0; f < NQ; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(pq + f * C.fstride));
+            }
+            const int64_t co = m + 1;
+            if (co >= s0 && co < s1) {
+                const int64_t oo = base + co * S;
+                if (A.acc_in == 2) {
+#pragma unroll
+                    for (int f = 0; f < NQ; ++f)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(A.rhsf + oo + f * C.fstride));
+                }
+                if (A.out_kind == 2) {
+#pragma unroll
+                    for (int f = 0; f < NQ; ++f)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(A.qn + oo + f * C.fstride));
+                }
+            }
+        }
         load_prim(m + 2, W[4]);
         R WRm[NQ], WLm[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k)
-            weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, WRm[k], WLm[k]);
+            weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
         if (m >= s0) {
             // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)
-            if (!physical_state<NF, ND, R>(WLprev, C) || !physical_state<NF, ND, R>(WRm, C)) {
+            if (!physical_state<NF, ND, R, MODE>(WLprev, C) || !physical_state<NF, ND, R, MODE>(WRm, C)) {
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     WLprev[k] = W[1][k];
@@ -84,15 +110,21 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
                 // finish cell m - 1 = window slot 1: faces m - 3/2 (Fprev) and m - 1/2 (F)
                 const int64_t off = base + (m - 1) * S;
                 const R du = uf - uprev;
+                // alpha rows: alpha div u, or (alpha + K) div u (Kapila)
+                R Kc = R(0);
+                if constexpr (NF == 2) {
+                    if (C.model == 1) Kc = kapila_K<MODE, R>(W[1][L::E], W[1][L::A], C);
+                }
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     R t;
+                    const R ac = (k >= L::A && C.model == 1) ? W[1][k] + Kc : W[1][k];
                     if constexpr (MODE == MODE_EXACT) {
                         t = (Fprev[k] - F[k]) / dx;
-                        if (k >= L::A) t = t + W[1][k] * du / dx;
+                        if (k >= L::A) t = t + ac * du / dx;
                     } else {
                         t = (Fprev[k] - F[k]) * inv_dx;
-                        if (k >= L::A) t = t + W[1][k] * du * inv_dx;
+                        if (k >= L::A) t = t + ac * du * inv_dx;
                     }
                     const int64_t o = off + k * C.fstride;
                     double Lc;
@@ -141,6 +173,174 @@ __global__ void __launch_bounds__(128, 4) sweep_kernel_mixed(const Consts C, con
     sweep_body<NF, ND, DIR, MODE_MIXED>(C, A);
 }
 
+// Value of neighbour lane + off (|off| <= 2) in the sequence formed by the
+// previous, current and next 32-cell chunks held by the warp (p, c, nx).
+template <class R>
+__device__ __forceinline__ R chunk_neighbour(R p, R c, R nx, int lane, int off) {
+    const int src = (lane + off) & 31;
+    const R inside = __shfl_sync(0xffffffffu, c, src);
+    const R outside = __shfl_sync(0xffffffffu, off < 0 ? p : nx, src);
+    return (lane + off >= 0 && lane + off < 32) ? inside : outside;
+}
+
+// x-direction sweep with one warp per line segment.  The warp walks the
+// segment in 32-cell chunks, lane l holding cell c = c0 + l: the primitive
+// state of every cell is computed once, the five-cell WENO stencil comes
+// from warp shuffles of the previous / current / next chunk, lane l solves
+// the face c - 1/2 (left state: the right edge value of lane l - 1) and
+// finishes cell c - 1 from its own face and lane l - 1's.  Loads and stores
+// along x are contiguous across the warp (the per-thread march of
+// sweep_body reads 32 rows at once along x and depends on L1 to keep them).
+// Same arithmetic, in the same order, as sweep_body.
+template <int NF, int ND, int MODE>
+__device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A) {
+    using L = Lay<NF, ND>;
+    using R = typename ModeT<MODE>::R;
+    constexpr int NQ = L::NQ;
+    const int lane = threadIdx.x & 31;
+    const int64_t nlines = C.n[1] * C.n[2];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nlines * A.nseg) return;  // whole warps only
+    const int64_t line = warp % nlines;
+    const int64_t seg = warp / nlines;
+    const int64_t ia = line % C.n[1], ib = line / C.n[1];
+    const int64_t base = C.origin + ia * C.stride[1] + ib * C.stride[2];
+    const int64_t S = C.stride[0];
+    const int64_t n = C.n[0];
+    const int64_t s0 = seg * A.seg;
+    const int64_t s1 = (s0 + A.seg < n) ? s0 + A.seg : n;
+    const int bclo = C.bc_lo[0], bchi = C.bc_hi[0];
+    const int variant = C.weno;
+    const R eps = sizeof(R) == 8 ? R(C.eps) : R(C.epsf);
+    const R ct = sizeof(R) == 8 ? R(C.teno_ct) : R(C.teno_ctf);
+    const R inv_dx = sizeof(R) == 8 ? R(C.inv_dx[0]) : R(C.inv_dxf[0]);
+    const double dx = C.dx[0];
+    const double dtv = (A.out_kind == 1 || A.out_kind == 2) ? *A.dt : 0.0;
+    bool bad = false;
+
+    // cells outside [-3, n + 2] are never needed; clamping keeps the lanes
+    // past the end of a segment on valid addresses
+    auto load_prim = [&](int64_t c, R* out) {
+        const bool need = c >= s0 - 3 && c <= s1 + 2;
+        c = c < -3 ? -3 : (c > n + 2 ? n + 2 : c);
+        bool flip = false;
+        const int64_t cc = bc_source(c, n, bclo, bchi, flip);
+        const double* p = A.q + base + cc * S;
+        double qc[NQ];
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * C.fstride);
+        if (flip) qc[L::MOM] = -qc[L::MOM];
+        bool b = false;
+        prim_for_recon<NF, ND, MODE, R>(qc, out, C, b);
+        bad |= need && b;
+    };
+
+    int64_t c0 = s0 - 1;
+    R Wp[NQ], Wc[NQ], Wn[NQ];
+    // lanes 30, 31 of the chunk before the first: cells s0 - 3, s0 - 2
+    load_prim(c0 - 32 + (lane < 30 ? 30 : lane), Wp);
+    load_prim(c0 + lane, Wc);
+    load_prim(c0 + 32 + lane, Wn);
+    R VRp[NQ], Fp[NQ], ufp = R(0);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        VRp[k] = Wp[k];
+        Fp[k] = R(0);
+    }
+
+    while (c0 <= s1) {
+        const int64_t c = c0 + lane;
+        R VL[NQ], VR[NQ], Wm1[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const R fm2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -2);
+            const R fm1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -1);
+            const R fp1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 1);
+            const R fp2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 2);
+            weno5_cell<MODE, R>(fm2, fm1, Wc[k], fp1, fp2, variant, eps, ct, VL[k], VR[k]);
+            Wm1[k] = fm1;
+        }
+        // face c - 1/2: left state = right edge value of cell c - 1
+        R WL[NQ], WR[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            WL[k] = chunk_neighbour(VRp[k], VR[k], VR[k], lane, -1);
+            WR[k] = VL[k];
+        }
+        const bool face = c >= s0 && c <= s1;
+        if (!physical_state<NF, ND, R, MODE>(WL, C) || !physical_state<NF, ND, R, MODE>(WR, C)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                WL[k] = Wm1[k];
+                WR[k] = Wc[k];
+            }
+        }
+        R F[NQ], uf;
+        bool fb = false;
+        hllc<NF, ND, 0, MODE>(WL, WR, C, F, uf, fb);
+        bad |= face && fb;
+        // finish cell c - 1 from faces c - 3/2 (lane - 1) and c - 1/2 (own)
+        const R ufm = chunk_neighbour(ufp, uf, uf, lane, -1);
+        const bool out = c - 1 >= s0 && c - 1 < s1;
+        const int64_t off = base + (c - 1) * S;
+        const R du = uf - ufm;
+        R Kc = R(0);
+        if constexpr (NF == 2) {
+            if (C.model == 1) Kc = kapila_K<MODE, R>(Wm1[L::E], Wm1[L::A], C);
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const R Fm = chunk_neighbour(Fp[k], F[k], F[k], lane, -1);
+            R t;
+            const R ac = (k >= L::A && C.model == 1) ? Wm1[k] + Kc : Wm1[k];
+            if constexpr (MODE == MODE_EXACT) {
+                t = (Fm - F[k]) / dx;
+                if (k >= L::A) t = t + ac * du / dx;
+            } else {
+                t = (Fm - F[k]) * inv_dx;
+                if (k >= L::A) t = t + ac * du * inv_dx;
+            }
+            if (!out) continue;
+            const int64_t o = off + k * C.fstride;
+            double Lc;
+            if constexpr (MODE == MODE_MIXED) {
+                const float Lf = (A.acc_in == 2) ? A.rhsf[o] + t : t;
+                if (A.out_kind == 3) {
+                    A.rhsf[o] = Lf;
+                    continue;
+                }
+                Lc = double(Lf);
+            } else {
+                Lc = A.acc_in ? A.rhs[o] + double(t) : double(t);
+            }
+            if (A.out_kind == 0) {
+                A.rhs[o] = Lc;
+            } else if (A.out_kind == 1) {
+                A.qout[o] = A.q[o] + dtv * Lc;
+            } else {
+                A.qout[o] = A.rk_a * A.qn[o] + A.rk_b * (A.q[o] + dtv * Lc);
+            }
+        }
+        // next chunk
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            Wp[k] = Wc[k];
+            Wc[k] = Wn[k];
+            VRp[k] = VR[k];
+            Fp[k] = F[k];
+        }
+        ufp = uf;
+        c0 += 32;
+        if (c0 <= s1) load_prim(c0 + 32 + lane, Wn);
+    }
+    if (bad) atomicOr(A.flag, 1);
+}
+
+template <int NF, int ND, int MODE>
+__global__ void __launch_bounds__(128) sweep_x_kernel(const Consts C, const SweepArgs A) {
+    sweep_x_body<NF, ND, MODE>(C, A);
+}
+
 // Interior linear index -> element offset in the padded layout.
 __device__ __forceinline__ int64_t interior_offset(const Consts& C, int64_t lin) {
     const int64_t i = lin % C.n[0];
@@ -174,7 +374,13 @@ __global__ void __launch_bounds__(256) cfl_kernel(const Consts C, const double* 
         for (int i = 1; i < NF; ++i) rho = rho + qc[i];
         double Gamma, Pi;
         mixture<NF, double>(qc + L::A, C, Gamma, Pi);
-        const double c2 = ((Gamma + 1.0) * w[L::E] + Pi) / (Gamma * rho);
+        double c2;
+        if constexpr (NF == 2) {
+            c2 = (C.model == 1) ? wood_c2<MODE_EXACT, double>(rho, w[L::E], w[L::A], C)
+                                : ((Gamma + 1.0) * w[L::E] + Pi) / (Gamma * rho);
+        } else {
+            c2 = ((Gamma + 1.0) * w[L::E] + Pi) / (Gamma * rho);
+        }
         bad |= !(c2 > 0.0);
         const double cs = sqrt(c2);
 #pragma unroll
@@ -234,10 +440,13 @@ __global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const dou
             ke = fma(qc[L::MOM + d], u[d], ke);
         }
         double Gamma, Pi;
-        mixture<NF, double>(qc + L::A, C, Gamma, Pi);
+        mixture_mode<NF, MODE_FAST, double>(qc + L::A, C, Gamma, Pi);
         const double iG = rcp_nr(Gamma);
         const double p = (qc[L::E] - 0.5 * ke - Pi) * iG;
-        const double c2 = ((Gamma + 1.0) * p + Pi) * iG * irho;
+        double c2 = ((Gamma + 1.0) * p + Pi) * iG * irho;
+        if constexpr (NF == 2) {
+            if (C.model == 1) c2 = wood_c2<MODE_FAST, double>(rho, p, qc[L::A], C);
+        }
         bad |= !(c2 > 0.0);
         const double cs = sqrt(c2);
         double smax = 0.0;

@@ -34,6 +34,22 @@ void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream
         sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
 }
 
+// x sweep, one warp per line segment (sweep_x_kernel): segments of at
+// least 64 cells, enough of them for ~32 warps per SM.
+template <int NF, int ND, int MODE>
+void launch_sweep_x(const Consts& C, SweepArgs A, cudaStream_t s) {
+    const int64_t nlines = C.n[1] * C.n[2];
+    const int64_t n = C.n[0];
+    int64_t nseg = (152LL * 32 + nlines - 1) / nlines;
+    const int64_t maxseg = (n + 63) / 64;
+    if (nseg > maxseg) nseg = maxseg;
+    if (nseg < 1) nseg = 1;
+    A.seg = (int)((n + nseg - 1) / nseg);
+    A.nseg = (int)((n + A.seg - 1) / A.seg);
+    const int64_t threads = nlines * A.nseg * 32;
+    sweep_x_kernel<NF, ND, MODE><<<grid_for(threads, kSweepBlock), kSweepBlock, 0, s>>>(C, A);
+}
+
 template <int NF, int ND, int DIR, int MODE>
 void launch_sweep_vjp(unsigned grid, const Consts& C, const VjpArgs& A, cudaStream_t s) {
     sweep_vjp_kernel<NF, ND, DIR, MODE><<<grid, kSweepVjpBlock, 0, s>>>(C, A);
@@ -53,10 +69,16 @@ cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream
         if constexpr (EXACT) {
             launch_sweep<NF, ND, D, MODE_EXACT>(grid, C, A, s);
         } else {
-            if (mode == MODE_MIXED)
-                launch_sweep<NF, ND, D, MODE_MIXED>(grid, C, A, s);
-            else
+            if (mode == MODE_MIXED) {
+                // float32 arithmetic is cheap enough that the x march's
+                // strided loads bound it: one warp per row instead
+                if constexpr (D == 0)
+                    launch_sweep_x<NF, ND, MODE_MIXED>(C, A, s);
+                else
+                    launch_sweep<NF, ND, D, MODE_MIXED>(grid, C, A, s);
+            } else {
                 launch_sweep<NF, ND, D, MODE_FAST>(grid, C, A, s);
+            }
         }
     };
     if (dir == 0) go(std::integral_constant<int, 0>());

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
     const bool periodic = bclo == BC_PERIODIC;
     const int variant = C.weno;
     const R eps = sizeof(R) == 8 ? R(C.eps) : R(C.epsf);
+    const R ct = sizeof(R) == 8 ? R(C.teno_ct) : R(C.teno_ctf);
     const R inv_dx = R(C.inv_dx[DIR]);
 
     R Wr[8][NQ];       // forward primitive states, ring indexed by cell & 7
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
         for (int k = 0; k < NQ; ++k) {
             R vl, vr;
             weno5_cell<MODE, R>(Wr[(jb - 2) & 7][k], Wr[(jb - 1) & 7][k], Wr[jb & 7][k], Wr[(jb + 1) & 7][k],
-                                Wr[(jb + 2) & 7][k], variant, eps, vl, vr);
+                                Wr[(jb + 2) & 7][k], variant, eps, ct, vl, vr);
             WLcur[k] = vr;
             WRbprev[k] = R(0);
         }
@@ -138,10 +139,10 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
 #pragma unroll
                 for (int k = 0; k < NQ; ++k)
                     weno5_cell<MODE, R>(Wr[(j - 1) & 7][k], Wr[j & 7][k], Wr[(j + 1) & 7][k], Wr[(j + 2) & 7][k],
-                                        Wr[(j + 3) & 7][k], variant, eps, WRj[k], WLnext[k]);
+                                        Wr[(j + 3) & 7][k], variant, eps, ct, WRj[k], WLnext[k]);
                 // first-order fallback of the forward pass at a non-physical face
                 const bool first_order =
-                    !physical_state<NF, ND, R>(WLcur, C) || !physical_state<NF, ND, R>(WRj, C);
+                    !physical_state<NF, ND, R, MODE>(WLcur, C) || !physical_state<NF, ND, R, MODE>(WRj, C);
                 if (first_order) {
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
@@ -154,10 +155,18 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) Fb[k] = (rbar(j + 1, k) - rbar(j, k)) * inv_dx;
                 R ufb = R(0);
+                // the alpha rows' coefficient of div u: alpha, or alpha + K (Kapila)
+                R Kj = R(0), Kj1 = R(0);
+                if constexpr (NF == 2) {
+                    if (C.model == 1) {
+                        Kj = kapila_K<MODE, R>(Wr[j & 7][L::E], Wr[j & 7][L::A], C);
+                        Kj1 = kapila_K<MODE, R>(Wr[(j + 1) & 7][L::E], Wr[(j + 1) & 7][L::A], C);
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < NF - 1; ++a) {
                     const int k = L::A + a;
-                    ufb += (rbar(j, k) * Wr[j & 7][k] - rbar(j + 1, k) * Wr[(j + 1) & 7][k]) * inv_dx;
+                    ufb += (rbar(j, k) * (Wr[j & 7][k] + Kj) - rbar(j + 1, k) * (Wr[(j + 1) & 7][k] + Kj1)) * inv_dx;
                 }
                 R uf;
                 hllc_adj<NF, ND, DIR, MODE>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     R f[5], fb[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
                     for (int m = 0; m < 5; ++m) f[m] = Wr[(j - 2 + m) & 7][k];
-                    weno5_cell_adj<MODE, R>(f, WRbprev[k], WLb[k], variant, eps, fb);
+                    weno5_cell_adj<MODE, R>(f, WRbprev[k], WLb[k], variant, eps, ct, fb);
 #pragma unroll
                     for (int m = 0; m < 5; ++m)
                         if (fb[m] != R(0)) sink(j - 2 + m, k, fb[m]);
@@ -204,9 +213,22 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     wb[k] = v;
                     qb[k] = 0.0;
                 }
-                cons_to_prim_adj<NF, ND, MODE>(qc, wb, C, qb);
-                // alpha_c (u_{c+1/2} - u_{c-1/2}) / dx
+                // alpha_c (u_{c+1/2} - u_{c-1/2}) / dx, and for the Kapila model
+                // K_c(p_c, alpha_c) (u_{c+1/2} - u_{c-1/2}) / dx
                 const double du = double(ufr[c & 7]) - double(ufr[(c - 1) & 7]);
+                if constexpr (NF == 2) {
+                    if (C.model == 1) {
+                        double w[NQ];
+                        bool b = false;
+                        cons_to_prim<NF, ND, (MODE == MODE_EXACT ? MODE_EXACT : MODE_FAST)>(qc, w, C, b);
+                        double dKdp, dKda;
+                        kapila_K_grad(w[L::E], w[L::A], C, dKdp, dKda);
+                        const double Kb = double(rbar(c, L::A)) * du * double(inv_dx);
+                        wb[L::E] += Kb * dKdp;
+                        wb[L::A] += Kb * dKda;
+                    }
+                }
+                cons_to_prim_adj<NF, ND, MODE>(qc, wb, C, qb);
 #pragma unroll
                 for (int a = 0; a < NF - 1; ++a) {
                     const int k = L::A + a;

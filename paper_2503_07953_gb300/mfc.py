@@ -26,7 +26,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmfcgb.so")
 MFC_OK, MFC_ERR_ARG, MFC_ERR_ALLOC, MFC_ERR_CUDA, MFC_ERR_NONPHYSICAL, MFC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE = 0, 1, 2
 MFC_FP64, MFC_MIXED, MFC_FP64_FAST = 0, 1, 2
-MFC_WENO_JS, MFC_WENO_M, MFC_WENO_Z = 0, 1, 2
+MFC_WENO_JS, MFC_WENO_M, MFC_WENO_Z, MFC_WENO_TENO = 0, 1, 2, 3
+MFC_MODEL_K0, MFC_MODEL_KAPILA = 0, 1
+MFC_RIEMANN_HLLC, MFC_RIEMANN_HLL = 0, 1
+MFC_LOW_MACH_NONE, MFC_LOW_MACH_THORNBER, MFC_LOW_MACH_APC = 0, 1, 2
 
 _STATUS = {0: "MFC_OK", -1: "MFC_ERR_ARG", -2: "MFC_ERR_ALLOC", -3: "MFC_ERR_CUDA",
            -4: "MFC_ERR_NONPHYSICAL", -5: "MFC_ERR_UNSUPPORTED"}
@@ -50,7 +53,8 @@ class mfc_eos(ctypes.Structure):
 
 class mfc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("weno", ctypes.c_int32), ("weno_eps", ctypes.c_double),
-                ("cfl", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("teno_ct", ctypes.c_double), ("model", ctypes.c_int32),
+                ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32)]
 
 
 _lib = None
@@ -184,7 +188,9 @@ class Solver:
                  lo: Optional[Sequence[float]] = None, hi: Optional[Sequence[float]] = None,
                  bc_lo: Optional[Sequence[int]] = None, bc_hi: Optional[Sequence[int]] = None,
                  ghost: int = 3, precision: int = MFC_FP64, weno: int = MFC_WENO_M,
-                 weno_eps: Optional[float] = None, cfl: float = 0.4, device=None):
+                 weno_eps: Optional[float] = None, cfl: float = 0.4, teno_ct: float = 1e-6,
+                 model: int = MFC_MODEL_K0, riemann: int = MFC_RIEMANN_HLLC,
+                 low_mach: int = MFC_LOW_MACH_NONE, device=None):
         nd = len(n)
         self.ndim, self.nf = nd, len(gamma)
         self.n = [int(x) for x in n] + [1] * (3 - nd)
@@ -210,6 +216,10 @@ class Solver:
         o.weno = int(weno)
         o.weno_eps = float(weno_eps if weno_eps is not None else (1e-6 if weno == MFC_WENO_JS else 1e-40))
         o.cfl = float(cfl)
+        o.teno_ct = float(teno_ct)
+        o.model = int(model)
+        o.riemann = int(riemann)
+        o.low_mach = int(low_mach)
         with torch.cuda.device(self.device):
             self.ctx = mfc_init(g, e, o)
         self.nq = mfc_num_fields(self.ctx)
@@ -221,7 +231,8 @@ class Solver:
     @classmethod
     def from_case(cls, case, **kw):
         return cls(case.n, case.gamma, case.pi_inf, lo=case.lo, hi=case.hi, bc_lo=case.bc_lo,
-                   bc_hi=case.bc_hi, weno=case.weno, weno_eps=case.eps, cfl=case.cfl, **kw)
+                   bc_hi=case.bc_hi, weno=case.weno, weno_eps=case.eps, cfl=case.cfl, teno_ct=case.teno_ct,
+                   model=case.model, riemann=case.riemann, low_mach=case.low_mach, **kw)
 
     # layout helpers
     def empty(self) -> torch.Tensor:

@@ -48,7 +48,7 @@ def _desc(mfc_lib, **over):
     e.gamma[0], e.gamma[1] = 1.4, 1.67
     o = mfc_lib.mfc_opts()
     o.precision, o.weno, o.weno_eps, o.cfl = 0, 1, 1e-40, 0.4
-    for k, v in over.items():
+    for k, v in sorted(over.items()):
         obj, field, val = v
         target = {"g": g, "e": e, "o": o}[obj]
         if isinstance(field, tuple):
@@ -69,9 +69,15 @@ def _desc(mfc_lib, **over):
     ({"x": ("e", ("gamma", 1), 1.0)}, "gamma"),
     ({"x": ("e", ("pi_inf", 0), -1.0)}, "pi_inf"),
     ({"x": ("o", "precision", 7)}, "precision"),
-    ({"x": ("o", "weno", 3)}, "WENO"),
+    ({"x": ("o", "weno", 4)}, "WENO"),
+    ({"x": ("o", "weno", 3), "y": ("o", "teno_ct", 1.5)}, "teno_ct"),
     ({"x": ("o", "weno_eps", 0.0)}, "weno_eps"),
     ({"x": ("o", "cfl", -0.1)}, "cfl"),
+    ({"x": ("o", "model", 2)}, "unknown model"),
+    ({"x": ("o", "riemann", 2)}, "Riemann"),
+    ({"x": ("o", "low_mach", 3)}, "low-Mach"),
+    ({"x": ("o", "low_mach", 2), "y": ("o", "riemann", 1)}, "needs HLLC"),
+    ({"x": ("o", "model", 1), "y": ("e", "nfluids", 3), "z": ("e", ("gamma", 2), 1.6)}, "Kapila"),
 ])
 def test_invalid_descriptions_rejected_on_host(mfc_lib, case, why):
     g, e, o = _desc(mfc_lib, **case)

@@ -52,6 +52,24 @@ def js(make, rho0=1.0, p0=1.0):
     return f
 
 
+def teno(cw):
+    case, W = cw
+    case.weno, case.eps = 3, 1e-40
+    return case, W
+
+
+def solver(cw, riemann, low_mach):
+    case, W = cw
+    case.riemann, case.low_mach = riemann, low_mach
+    return case, W
+
+
+def kapila(cw):
+    case, W = cw
+    case.model = 1
+    return case, W
+
+
 def stiff_smooth_case(dims=(13, 11), seed=4):
     """Smooth water-like / air-like mixture at 1e9 Pa, moving at ~100 m/s."""
     nd = len(dims)
@@ -71,12 +89,17 @@ CASES = {
     "smooth_3d_mixed_bc": lambda: smooth_case((11, 9, 7), (0, 1, 2), (0, 2, 1)),
     "stiff_smooth_2d": stiff_smooth_case,
     "smooth_2d_periodic": lambda: smooth_case((19, 17), (0, 0), (0, 0)),
+    "smooth_2d_teno": lambda: teno(smooth_case((19, 17), (0, 1), (0, 2))),
+    "smooth_2d_kapila": lambda: kapila(smooth_case((19, 17), (1, 0), (2, 0))),
+    "smooth_2d_hll_thornber": lambda: solver(smooth_case((19, 17), (0, 1), (0, 2)), 1, 1),
+    "smooth_2d_apc": lambda: solver(smooth_case((19, 17), (2, 0), (1, 0)), 0, 2),
     "shock_bubble_3d_js": js(lambda: wl.shock_bubble_3d(dims=(21, 18, 17))),
     "water_air_1d_js": js(lambda: wl.water_air_shock_tube(300), 1000.0, 1e9),
     "random_interfaces_js": js(lambda: wl.random_interfaces_window(dims=(12, 11, 10)), 1000.0, 1e5),
     "bubble_collapse_2d_js": js(lambda: wl.bubble_collapse_2d(dims=(24, 22)), 1000.0, 1e7),
 }
-SMOOTH = ["smooth_3d_mixed_bc", "smooth_2d_periodic", "stiff_smooth_2d"]
+SMOOTH = ["smooth_3d_mixed_bc", "smooth_2d_periodic", "stiff_smooth_2d", "smooth_2d_teno", "smooth_2d_kapila",
+          "smooth_2d_hll_thornber", "smooth_2d_apc"]
 PARAMS = [(name, 0) for name in sorted(CASES)] + [(name, 2) for name in SMOOTH]
 
 
@@ -135,6 +158,8 @@ def full_jacobians(oracle_lib, S, P, q):
     return J, JT
 
 
+@pytest.mark.parametrize("model,riemann,low_mach", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (0, 0, 2),
+                                                    (0, 1, 1), (1, 0, 2)])
 @pytest.mark.parametrize("dims,bc_lo,bc_hi", [
     ((17,), (2,), (2,)),        # two segments, the second one cell long, reflective
     ((19,), (0,), (0,)),        # periodic with two segments
@@ -142,10 +167,13 @@ def full_jacobians(oracle_lib, S, P, q):
     ((6, 5), (0, 2), (0, 1)),   # 2D, every boundary type
     ((3, 4), (0, 1), (0, 1)),   # smallest periodic axis
 ])
-def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi):
+def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi, model, riemann, low_mach):
     """Every column of dL/dq from the oracle's dual numbers equals every row
-    of the GPU adjoint: the transposed Jacobian matches entry by entry."""
+    of the GPU adjoint: the transposed Jacobian matches entry by entry
+    (model 1: the Kapila K div u term and the Wood sound speed; riemann 1:
+    HLL; low_mach 1, 2: Thornber, anti-dissipation pressure correction)."""
     case, W = smooth_case(dims, bc_lo, bc_hi)
+    case.model, case.riemann, case.low_mach = model, riemann, low_mach
     P = oracle_problem(oracle_lib, case)
     S = solver_for(mfc_lib, case)
     q = oracle_lib.prim_to_cons(P, W)
@@ -154,7 +182,8 @@ def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi)
 
 
 @pytest.mark.parametrize("name,weno", [("water_air", 1), ("water_air", 0), ("bubble", 1), ("bubble", 0),
-                                       ("shock_bubble", 1), ("stiff_smooth", 1), ("stiff_smooth", 0)])
+                                       ("shock_bubble", 1), ("stiff_smooth", 1), ("stiff_smooth", 0),
+                                       ("water_air", 3), ("shock_bubble", 3), ("stiff_smooth", 3)])
 def test_rhs_full_jacobian_workload_states(oracle_lib, mfc_lib, cuda_device, name, weno):
     """Entry by entry on tiny versions of the workloads' initial states
     (stiff interfaces, fluid at rest, sharp jumps), MFC_FP64: the same

@@ -98,7 +98,7 @@ def test_step_mixed(oracle_lib, mfc_lib, cuda_device, name):
     assert (err <= 1e-4).all(), err
 
 
-@pytest.mark.parametrize("weno", [0, 2])
+@pytest.mark.parametrize("weno", [0, 2, 3])
 @pytest.mark.parametrize("prec", [0, 2])
 def test_rhs_weno_variants(oracle_lib, mfc_lib, cuda_device, weno, prec):
     case, W = wl.shock_bubble_3d(dims=(19, 16, 14))
@@ -153,6 +153,114 @@ def test_rk3_run_bitwise(oracle_lib, mfc_lib, cuda_device, name):
     assert np.array_equal(dt_log.cpu().numpy(), dts)
     got = to_host(S, q_g)
     assert np.array_equal(got, q_end), case_errors(case, got, q_end)
+
+
+@pytest.mark.parametrize("name", ["shock_bubble_3d", "water_air_1d"])
+def test_rk3_run_teno_bitwise(oracle_lib, mfc_lib, cuda_device, name):
+    """TENO weights (Sec. 4.2.2), MFC_FP64: 50 CFL steps bit for bit."""
+    make, _ = RUNS[name]
+    case, W = make()
+    case.weno = 3
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    q_g = S.from_interior(q_o)
+    S.rk3_run(q_g, 50, 0.0)
+    S.check()
+    q_end, _ = oracle_lib.rk3_run(P, q_o, 50, cfl=case.cfl)
+    got = to_host(S, q_g)
+    assert np.array_equal(got, q_end), case_errors(case, got, q_end)
+
+
+def kapila_pulse(n=400):
+    """A small pressure pulse in a 50/50 water / air mixture at rest."""
+    case = wl.Case("pulse", [n], [0.0], [1.0], [wl.PERIODIC], [wl.PERIODIC], [4.4, 1.4], [6e8, 0.0], 0.4, 0)
+    case.model = 1
+    X, _, _ = wl._centres(case)
+    p = 1e5 * (1 + 1e-3 * np.exp(-((X - 0.5) / 0.03) ** 2))
+    rho = [1000.0 * ((p + 6e8) / (1e5 + 6e8)) ** (1 / 4.4), 1.2 * (p / 1e5) ** (1 / 1.4)]
+    a = np.full_like(X, 0.5)
+    return case, wl._assemble(case, [a, 1 - a], rho, [np.zeros_like(X)], p)
+
+
+def kapila_shock_bubble():
+    case, W = wl.shock_bubble_3d(dims=(20, 18, 16))
+    case.model = 1
+    return case, W
+
+
+@pytest.mark.parametrize("make,steps", [(kapila_pulse, 100), (kapila_shock_bubble, 50)])
+def test_rk3_run_kapila_bitwise(oracle_lib, mfc_lib, cuda_device, make, steps):
+    """The Kapila K div u term with the Wood sound speed (Sec. 2.1.1),
+    MFC_FP64: CFL steps bit for bit, dt sequence included."""
+    case, W = make()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    q_g = S.from_interior(q_o)
+    dt_log = torch.zeros(steps, dtype=torch.float64, device=cuda_device)
+    S.rk3_run(q_g, steps, 0.0, dt_log)
+    S.check()
+    q_end, dts, bad = oracle_lib.rk3_run(P, q_o, steps, cfl=case.cfl, return_bad=True)
+    assert bad == 0
+    assert np.array_equal(dt_log.cpu().numpy(), dts)
+    got = to_host(S, q_g)
+    assert np.array_equal(got, q_end), case_errors(case, got, q_end)
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 1e-11), (1, 1e-4)])
+def test_step_kapila_fast_and_mixed(oracle_lib, mfc_lib, cuda_device, prec, tol):
+    case, W = kapila_shock_bubble()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    dt = oracle_lib.cfl_dt(P, q_o, case.cfl)
+    q = S.from_interior(q_o)
+    S.rk3_step(q, dt)
+    S.check()
+    err = case_errors(case, to_host(S, q), oracle_lib.rk3_step(P, q_o, dt))
+    assert (err <= tol).all(), err
+
+
+SOLVERS = [(1, 0), (0, 1), (0, 2), (1, 1)]  # (riemann, low_mach): HLL, HLLC+Thornber, HLLC+APC, HLL+Thornber
+
+
+@pytest.mark.parametrize("riemann,low_mach", SOLVERS)
+def test_rk3_run_riemann_variants_bitwise(oracle_lib, mfc_lib, cuda_device, riemann, low_mach):
+    """HLL and the low-Mach corrections (Sec. 3.2.2, Sec. 4.2.4), MFC_FP64:
+    the Gresho vortex at M = 0.01 (40 steps) and the shock-bubble
+    (20 steps), bit for bit with their dt sequences."""
+    for make, steps in ((lambda: wl.gresho_vortex(24, 1e-2), 40), (lambda: wl.shock_bubble_3d(dims=(16, 14, 12)), 20)):
+        case, W = make()
+        case.riemann, case.low_mach = riemann, low_mach
+        P = oracle_problem(oracle_lib, case)
+        S = solver_for(mfc_lib, case)
+        q_o = oracle_lib.prim_to_cons(P, W)
+        q_g = S.from_interior(q_o)
+        dt_log = torch.zeros(steps, dtype=torch.float64, device=cuda_device)
+        S.rk3_run(q_g, steps, 0.0, dt_log)
+        S.check()
+        q_end, dts, bad = oracle_lib.rk3_run(P, q_o, steps, cfl=case.cfl, return_bad=True)
+        assert bad == 0
+        assert np.array_equal(dt_log.cpu().numpy(), dts)
+        got = to_host(S, q_g)
+        assert np.array_equal(got, q_end), case_errors(case, got, q_end)
+
+
+@pytest.mark.parametrize("riemann,low_mach", SOLVERS)
+@pytest.mark.parametrize("prec,tol", [(2, 1e-11), (1, 1e-4)])
+def test_step_riemann_variants_fast_and_mixed(oracle_lib, mfc_lib, cuda_device, riemann, low_mach, prec, tol):
+    case, W = wl.shock_bubble_3d(dims=(16, 14, 12))
+    case.riemann, case.low_mach = riemann, low_mach
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    dt = oracle_lib.cfl_dt(P, q_o, case.cfl)
+    q = S.from_interior(q_o)
+    S.rk3_step(q, dt)
+    S.check()
+    err = case_errors(case, to_host(S, q), oracle_lib.rk3_step(P, q_o, dt))
+    assert (err <= tol).all(), err
 
 
 def test_rk3_run_fast_shock_bubble(oracle_lib, mfc_lib, cuda_device):
