@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "../../include/mfc.h"
 #include "mfc_launch.h"
@@ -42,6 +43,10 @@ struct mfc_ctx {
     double* a1 = nullptr;
     double* a2 = nullptr;
     double* a3 = nullptr;
+    // x <-> y transposed copies for the x adjoint sweep (allocated on first use)
+    double* t1 = nullptr;
+    double* t2 = nullptr;
+    double* t3 = nullptr;
     DevScalars* scal = nullptr;
     std::string err;
 };
@@ -76,6 +81,36 @@ __global__ void finalize_dt_kernel(DevScalars* s, double cfl, double* dt_out) {
 }
 
 __global__ void copy_dt_kernel(const DevScalars* s, double* dt_out) { *dt_out = s->dt; }
+
+// dst = src (add = 0) or dst += src (add = 1) with the x and y axes of the
+// interior swapped and the fields of the x and y momenta swapped: cell
+// (i, j, k) of src (layout Cs) goes to cell (j, i, k) of dst (layout Cd).
+// 32 x 32 tiles through shared memory, so that both sides are read and
+// written along their own fastest axis.
+__global__ void __launch_bounds__(256) transpose_xy_kernel(const mfc::Consts Cs, const mfc::Consts Cd,
+                                                           const double* src, double* dst, int add, int mom0) {
+    __shared__ double tile[32][33];
+    const int64_t nx = Cs.n[0], ny = Cs.n[1];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int64_t kf = blockIdx.z;  // field * nz + k
+    const int64_t k = kf % Cs.n[2];
+    const int f = (int)(kf / Cs.n[2]);
+    const int fd = (f == mom0) ? mom0 + 1 : ((f == mom0 + 1) ? mom0 : f);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + tx, j = j0 + r;
+        if (i < nx && j < ny)
+            tile[r][tx] = src[f * Cs.fstride + Cs.origin + i * Cs.stride[0] + j * Cs.stride[1] + k * Cs.stride[2]];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + tx, i = i0 + r;  // dst cell (j, i, k)
+        if (i < nx && j < ny) {
+            double* p = dst + fd * Cd.fstride + Cd.origin + j * Cd.stride[0] + i * Cd.stride[1] + k * Cd.stride[2];
+            *p = add ? *p + tile[tx][r] : tile[tx][r];
+        }
+    }
+}
 
 // out = a x + b y + c z on the interior cells of every field (y, z may be
 // null when their coefficient is 0).  Element-wise, so out may alias x, y or z.
@@ -297,15 +332,82 @@ mfc_status lincomb(mfc_ctx* ctx, double* out, double a, const double* x, double 
 }
 
 // qbar += (dL/dq)^T rbar: one adjoint sweep per direction.
+// The constants of the same grid with the x and y axes swapped.
+mfc::Consts transposed_xy(const mfc::Consts& C) {
+    mfc::Consts T = C;
+    std::swap(T.n[0], T.n[1]);
+    std::swap(T.bc_lo[0], T.bc_lo[1]);
+    std::swap(T.bc_hi[0], T.bc_hi[1]);
+    std::swap(T.dx[0], T.dx[1]);
+    std::swap(T.inv_dx[0], T.inv_dx[1]);
+    std::swap(T.inv_dxf[0], T.inv_dxf[1]);
+    // padded extents: x of T is y of C and vice versa (ghost width g on both)
+    const int64_t px = C.stride[1], py = C.stride[2] / C.stride[1];
+    const int64_t g = (px - C.n[0]) / 2;
+    T.stride[0] = 1;
+    T.stride[1] = py;
+    T.stride[2] = C.stride[2];
+    T.origin = g * T.stride[0] + g * T.stride[1] + (C.origin - g * C.stride[0] - g * C.stride[1]);
+    return T;
+}
+
+mfc_status ensure_transpose_scratch(mfc_ctx* ctx) {
+    if (ctx->t1) return MFC_OK;
+    const size_t bytes = (size_t)ctx->total * sizeof(double);
+    if (cudaMalloc(&ctx->t1, bytes) != cudaSuccess || cudaMalloc(&ctx->t2, bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->t3, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        for (double** p : {&ctx->t1, &ctx->t2, &ctx->t3}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        return fail(ctx, MFC_ERR_ALLOC, "device allocation of the adjoint transpose scratch failed");
+    }
+    return MFC_OK;
+}
+
+mfc_status transpose_xy(mfc_ctx* ctx, const mfc::Consts& Cs, const mfc::Consts& Cd, const double* src, double* dst,
+                        int add, cudaStream_t s) {
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((Cs.n[0] + 31) / 32), (unsigned)((Cs.n[1] + 31) / 32),
+                    (unsigned)(Cs.n[2] * Cs.nq));
+    transpose_xy_kernel<<<grid, block, 0, s>>>(Cs, Cd, src, dst, add, Cs.nf);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MFC_OK : cuda_fail(ctx, e, "transpose kernel");
+}
+
+// qbar += (dL/dq)^T rbar: one adjoint sweep per direction.  In 2D and 3D
+// the x sweep runs as a y sweep on x <-> y transposed copies of q, rbar and
+// its own bar: the per-thread march along x reads 32 rows at once and
+// thrashes L1, the y march reads rows whole (the result is the same
+// arithmetic on the same values).
 mfc_status eval_L_vjp(mfc_ctx* ctx, const double* q, const double* rbar, double* qbar, cudaStream_t s) {
-    for (int d = 0; d < ctx->C.nd; ++d) {
+    const mfc::Consts& C = ctx->C;
+    for (int d = 0; d < C.nd; ++d) {
         mfc::VjpArgs A;
         std::memset(&A, 0, sizeof(A));
+        cudaError_t e;
+        if (d == 0 && C.nd >= 2) {
+            mfc_status st = ensure_transpose_scratch(ctx);
+            if (st != MFC_OK) return st;
+            const mfc::Consts T = transposed_xy(C);
+            if ((st = transpose_xy(ctx, C, T, q, ctx->t1, 0, s)) != MFC_OK) return st;
+            if ((st = transpose_xy(ctx, C, T, rbar, ctx->t2, 0, s)) != MFC_OK) return st;
+            if ((e = cudaMemsetAsync(ctx->t3, 0, (size_t)ctx->total * sizeof(double), s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "clear transposed bar");
+            A.q = ctx->t1;
+            A.rbar = ctx->t2;
+            A.qbar = ctx->t3;
+            if ((e = ctx->fns->sweep_vjp(T, 1, ctx->mode, A, s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "adjoint sweep kernel");
+            if ((st = transpose_xy(ctx, T, C, ctx->t3, qbar, 1, s)) != MFC_OK) return st;
+            continue;
+        }
         A.q = q;
         A.rbar = rbar;
         A.qbar = qbar;
-        cudaError_t e = ctx->fns->sweep_vjp(ctx->C, d, ctx->mode, A, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint sweep kernel");
+        if ((e = ctx->fns->sweep_vjp(C, d, ctx->mode, A, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "adjoint sweep kernel");
     }
     return MFC_OK;
 }
@@ -405,7 +507,7 @@ mfc_status mfc_destroy(mfc_ctx* ctx) {
     if (!ctx) return MFC_OK;
     DeviceGuard guard(ctx->device);
     cudaDeviceSynchronize();
-    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3})
+    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3, ctx->t1, ctx->t2, ctx->t3})
         if (p) cudaFree(p);
     if (ctx->scal) cudaFree(ctx->scal);
     delete ctx;

@@ -12,6 +12,9 @@
 namespace mfc {
 
 constexpr int kSweepBlock = 128;
+// Below this many lines the per-thread march along x leaves the GPU idle
+// (a 1D run is one line): the x sweep then runs one warp per segment.
+constexpr int64_t kFewLines = 2048;
 constexpr int kSweepVjpBlock = 64;
 
 inline unsigned grid_for(int64_t threads, int block) {
@@ -35,13 +38,15 @@ void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream
 }
 
 // x sweep, one warp per line segment (sweep_x_kernel): segments of at
-// least 64 cells, enough of them for ~32 warps per SM.
+// least 64 cells (32 when there are few lines), enough of them for ~32 warps
+// per SM.
 template <int NF, int ND, int MODE>
 void launch_sweep_x(const Consts& C, SweepArgs A, cudaStream_t s) {
     const int64_t nlines = C.n[1] * C.n[2];
     const int64_t n = C.n[0];
     int64_t nseg = (152LL * 32 + nlines - 1) / nlines;
-    const int64_t maxseg = (n + 63) / 64;
+    const int64_t minseg = nlines < kFewLines ? 32 : 64;
+    const int64_t maxseg = (n + minseg - 1) / minseg;
     if (nseg > maxseg) nseg = maxseg;
     if (nseg < 1) nseg = 1;
     A.seg = (int)((n + nseg - 1) / nseg);
@@ -52,7 +57,8 @@ void launch_sweep_x(const Consts& C, SweepArgs A, cudaStream_t s) {
 
 template <int NF, int ND, int DIR, int MODE>
 void launch_sweep_vjp(unsigned grid, const Consts& C, const VjpArgs& A, cudaStream_t s) {
-    sweep_vjp_kernel<NF, ND, DIR, MODE><<<grid, kSweepVjpBlock, 0, s>>>(C, A);
+    sweep_vjp_kernel<NF, ND, DIR, MODE>
+        <<<grid, kSweepVjpBlock, vjp_smem_bytes<NF, ND, MODE>(kSweepVjpBlock), s>>>(C, A);
 }
 
 // MODE_EXACT when EXACT, else MODE_FAST / MODE_MIXED as asked.
@@ -66,17 +72,31 @@ cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream
     const unsigned grid = grid_for(threads, kSweepBlock);
     auto go = [&](auto dirc) {
         constexpr int D = decltype(dirc)::value;
+        // x sweeps run one warp per row in the mixed mode (float32 arithmetic
+        // is cheap enough that the x march's strided loads bound it) and for
+        // few lines (the march would leave most of the GPU idle)
+        const bool few = nlines < kFewLines;
         if constexpr (EXACT) {
+            if constexpr (D == 0) {
+                if (few) {
+                    launch_sweep_x<NF, ND, MODE_EXACT>(C, A, s);
+                    return;
+                }
+            }
             launch_sweep<NF, ND, D, MODE_EXACT>(grid, C, A, s);
         } else {
             if (mode == MODE_MIXED) {
-                // float32 arithmetic is cheap enough that the x march's
-                // strided loads bound it: one warp per row instead
                 if constexpr (D == 0)
                     launch_sweep_x<NF, ND, MODE_MIXED>(C, A, s);
                 else
                     launch_sweep<NF, ND, D, MODE_MIXED>(grid, C, A, s);
             } else {
+                if constexpr (D == 0) {
+                    if (few) {
+                        launch_sweep_x<NF, ND, MODE_FAST>(C, A, s);
+                        return;
+                    }
+                }
                 launch_sweep<NF, ND, D, MODE_FAST>(grid, C, A, s);
             }
         }

@@ -17,6 +17,13 @@ namespace mfc {
 // ghost copies (normal momentum negated across a reflective wall); for a
 // periodic axis the segments that own the copied cells collect those
 // contributions in a short pass over the far end of the line first.
+// Dynamic shared memory of one sweep_vjp_kernel block (the rings of the
+// float32 mode; none for the float64 modes).
+template <int NF, int ND, int MODE>
+constexpr size_t vjp_smem_bytes(int block) {
+    return MODE == MODE_MIXED ? size_t(16 * Lay<NF, ND>::NQ + 8) * block * sizeof(float) : 0;
+}
+
 template <int NF, int ND, int DIR, int MODE>
 __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
     using L = Lay<NF, ND>;
@@ -44,9 +51,30 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
     const R ct = sizeof(R) == 8 ? R(C.teno_ct) : R(C.teno_ctf);
     const R inv_dx = R(C.inv_dx[DIR]);
 
-    R Wr[8][NQ];       // forward primitive states, ring indexed by cell & 7
-    R acc[8][NQ];      // primitive-state bars, same ring
-    R ufr[8];          // forward face velocities, ring indexed by face & 7
+    // rings indexed by cell & 7 (face & 7 for the face velocities): forward
+    // primitive states, their bars, forward face velocities.  The float32
+    // mode keeps them in shared memory, interleaved by thread so that a warp
+    // touches 32 consecutive words (vjp_smem_bytes); the float64 modes in
+    // local memory.
+    constexpr bool kSmem = MODE == MODE_MIXED;
+    extern __shared__ unsigned char vjp_smem[];
+    R* const sm = reinterpret_cast<R*>(vjp_smem);
+    const int tix = threadIdx.x, bdim = blockDim.x;
+    R Wr_l[kSmem ? 1 : 8][NQ];
+    R acc_l[kSmem ? 1 : 8][NQ];
+    R ufr_l[kSmem ? 1 : 8];
+    auto WR = [&](int64_t slot, int k) -> R& {
+        if constexpr (kSmem) return sm[((slot & 7) * NQ + k) * bdim + tix];
+        else return Wr_l[slot & 7][k];
+    };
+    auto ACC = [&](int64_t slot, int k) -> R& {
+        if constexpr (kSmem) return sm[((8 + (slot & 7)) * NQ + k) * bdim + tix];
+        else return acc_l[slot & 7][k];
+    };
+    auto UFR = [&](int64_t slot) -> R& {
+        if constexpr (kSmem) return sm[(16 * NQ + (slot & 7)) * bdim + tix];
+        else return ufr_l[slot & 7];
+    };
     R ext_lo[3][NQ];   // periodic: bars of ghosts n..n+2, i.e. of cells 0..2
     R ext_hi[3][NQ];   // periodic: bars of ghosts -3..-1, i.e. of cells n-3..n-1
 #pragma unroll
@@ -64,6 +92,12 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * fs);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
         prim_for_recon<NF, ND, MODE, R>(qc, out, C, bad);
+    };
+    auto load_ring = [&](int64_t c) {
+        R w[NQ];
+        load_prim(c, w);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) WR(c, k) = w[k];
     };
     auto rbar = [&](int64_t c, int k) -> R {
         return (c >= 0 && c < n) ? R(__ldg(A.rbar + base + c * S + k * fs)) : R(0);
@@ -102,34 +136,34 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
             } else if (pass == 1) {
                 if (x >= -3 && x < 0) ext_hi[x + 3][k] += v;
             } else if (x >= 0 && x < n) {
-                acc[x & 7][k] += v;
+                ACC(x, k) += v;
             } else if (!periodic) {
                 bool flip = false;
                 const int64_t img = bc_source(x, n, bclo, bchi, flip);
-                acc[img & 7][k] += (flip && k == L::MOM + DIR) ? -v : v;
+                ACC(img, k) += (flip && k == L::MOM + DIR) ? -v : v;
             }
         };
 #pragma unroll
         for (int s = 0; s < 8; ++s)
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) acc[s][k] = R(0);
-        for (int64_t c = jb - 2; c <= jb + 2; ++c) load_prim(c, Wr[c & 7]);
+            for (int k = 0; k < NQ; ++k) ACC(s, k) = R(0);
+        for (int64_t c = jb - 2; c <= jb + 2; ++c) load_ring(c);
         // forward left state of face jb (right edge of cell jb)
         R WLcur[NQ], WRbprev[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             R vl, vr;
-            weno5_cell<MODE, R>(Wr[(jb - 2) & 7][k], Wr[(jb - 1) & 7][k], Wr[jb & 7][k], Wr[(jb + 1) & 7][k],
-                                Wr[(jb + 2) & 7][k], variant, eps, ct, vl, vr);
+            weno5_cell<MODE, R>(WR(jb - 2, k), WR(jb - 1, k), WR(jb, k), WR(jb + 1, k), WR(jb + 2, k), variant, eps,
+                                ct, vl, vr);
             WLcur[k] = vr;
             WRbprev[k] = R(0);
         }
         for (int64_t j = jb; j <= je; ++j) {
             const bool face = (j >= -1) && (j <= fmax);
             const bool cellw = (j >= cmin) && (j <= cmax);
-            if (face) load_prim(j + 3, Wr[(j + 3) & 7]);  // j + 3 <= n + 2
+            if (face) load_ring(j + 3);  // j + 3 <= n + 2
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) acc[(j + 3) & 7][k] = R(0);
+            for (int k = 0; k < NQ; ++k) ACC(j + 3, k) = R(0);
             R WLb[NQ], WRb[NQ], WLnext[NQ];
 #pragma unroll
             for (int k = 0; k < NQ; ++k) WLb[k] = WRb[k] = R(0);
@@ -138,16 +172,16 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 R WRj[NQ];
 #pragma unroll
                 for (int k = 0; k < NQ; ++k)
-                    weno5_cell<MODE, R>(Wr[(j - 1) & 7][k], Wr[j & 7][k], Wr[(j + 1) & 7][k], Wr[(j + 2) & 7][k],
-                                        Wr[(j + 3) & 7][k], variant, eps, ct, WRj[k], WLnext[k]);
+                    weno5_cell<MODE, R>(WR(j - 1, k), WR(j, k), WR(j + 1, k), WR(j + 2, k), WR(j + 3, k), variant, eps,
+                                        ct, WRj[k], WLnext[k]);
                 // first-order fallback of the forward pass at a non-physical face
                 const bool first_order =
                     !physical_state<NF, ND, R, MODE>(WLcur, C) || !physical_state<NF, ND, R, MODE>(WRj, C);
                 if (first_order) {
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
-                        WLcur[k] = Wr[j & 7][k];
-                        WRj[k] = Wr[(j + 1) & 7][k];
+                        WLcur[k] = WR(j, k);
+                        WRj[k] = WR(j + 1, k);
                     }
                 }
                 // bars of the face flux and face velocity from rbar of cells j and j+1
@@ -159,18 +193,18 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 R Kj = R(0), Kj1 = R(0);
                 if constexpr (NF == 2) {
                     if (C.model == 1) {
-                        Kj = kapila_K<MODE, R>(Wr[j & 7][L::E], Wr[j & 7][L::A], C);
-                        Kj1 = kapila_K<MODE, R>(Wr[(j + 1) & 7][L::E], Wr[(j + 1) & 7][L::A], C);
+                        Kj = kapila_K<MODE, R>(WR(j, L::E), WR(j, L::A), C);
+                        Kj1 = kapila_K<MODE, R>(WR(j + 1, L::E), WR(j + 1, L::A), C);
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < NF - 1; ++a) {
                     const int k = L::A + a;
-                    ufb += (rbar(j, k) * (Wr[j & 7][k] + Kj) - rbar(j + 1, k) * (Wr[(j + 1) & 7][k] + Kj1)) * inv_dx;
+                    ufb += (rbar(j, k) * (WR(j, k) + Kj) - rbar(j + 1, k) * (WR(j + 1, k) + Kj1)) * inv_dx;
                 }
                 R uf;
                 hllc_adj<NF, ND, DIR, MODE>(WLcur, WRj, C, Fb, ufb, WLb, WRb, uf);
-                ufr[j & 7] = uf;
+                UFR(j) = uf;
                 if (first_order) {
                     // the face states are the cell states themselves
 #pragma unroll
@@ -181,7 +215,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     }
                 }
             } else {
-                ufr[j & 7] = R(0);
+                UFR(j) = R(0);
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) WLnext[k] = R(0);
             }
@@ -192,7 +226,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 for (int k = 0; k < NQ; ++k) {
                     R f[5], fb[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
-                    for (int m = 0; m < 5; ++m) f[m] = Wr[(j - 2 + m) & 7][k];
+                    for (int m = 0; m < 5; ++m) f[m] = WR(j - 2 + m, k);
                     weno5_cell_adj<MODE, R>(f, WRbprev[k], WLb[k], variant, eps, ct, fb);
 #pragma unroll
                     for (int m = 0; m < 5; ++m)
@@ -207,7 +241,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     qc[k] = __ldg(A.q + off + k * fs);
-                    double v = double(acc[c & 7][k]);
+                    double v = double(ACC(c, k));
                     if (periodic && c < 3) v += double(ext_lo[c][k]);
                     if (periodic && c >= n - 3) v += double(ext_hi[c - (n - 3)][k]);
                     wb[k] = v;
@@ -215,7 +249,7 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 }
                 // alpha_c (u_{c+1/2} - u_{c-1/2}) / dx, and for the Kapila model
                 // K_c(p_c, alpha_c) (u_{c+1/2} - u_{c-1/2}) / dx
-                const double du = double(ufr[c & 7]) - double(ufr[(c - 1) & 7]);
+                const double du = double(UFR(c)) - double(UFR(c - 1));
                 if constexpr (NF == 2) {
                     if (C.model == 1) {
                         double w[NQ];
