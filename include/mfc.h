@@ -188,6 +188,33 @@ mfc_status mfc_rk3_step(mfc_ctx* ctx, double* q, double dt, double* dt_used, voi
  * fixed dt.  dt_log (nullable) is a DEVICE array of nsteps doubles. */
 mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, double* dt_log, void* stream);
 
+/* One mfc_rk3_step (Sec. 3.4) of each of `count` independent states held
+ * in HOST memory, with the copies overlapped with the steps.  q_in[b] and
+ * q_out[b] are host buffers of mfc_num_fields() x mfc_field_stride()
+ * doubles in the layout above (ghost entries are copied through
+ * unchanged); state b is read from q_in[b], stepped, and written to
+ * q_out[b].  q_in and q_out are host arrays of count pointers.
+ *
+ * The context stages the states through two device states of its own
+ * (allocated on the first call: twice the state size) on two copy streams
+ * of its own: while state b is stepped on `stream`, state b+1 is uploaded
+ * and state b-1 downloaded.  Uploads run in the order of b, downloads too.
+ * So a host buffer may be read as several q_in[b] and written as several
+ * q_out[b] (it ends holding the last), and q_out[b] may be q_in[b]; a
+ * buffer written as q_out[b] must not be read as q_in[b'] for b' != b.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the
+ * copies overlap the steps; pageable memory gives the same results with
+ * the copies serialised.
+ *
+ * dt as for mfc_rk3_step, per state (dt <= 0: each state's own CFL dt).
+ * dt_used (nullable) is a HOST array of count doubles.  The call returns
+ * when every result is in host memory, with `stream` synchronised, and
+ * reports a non-physical state as mfc_check does.  count == 0 does
+ * nothing; a null array or element, count < 0 or a non-finite dt is
+ * MFC_ERR_ARG before any copy. */
+mfc_status mfc_rk3_step_batch_host(mfc_ctx* ctx, int32_t count, const double* const* q_in, double* const* q_out,
+                                   double dt, double* dt_used, void* stream);
+
 /* Adjoint of mfc_rhs: q_bar += (dL/dq)^T rhs_bar, interior cells.  rhs_bar
  * and q_bar are state-sized device buffers; q_bar must not alias q or
  * rhs_bar.  Non-smooth points (min/max of wave speeds, the HLLC side, |.|

@@ -47,6 +47,17 @@ struct mfc_ctx {
     double* t1 = nullptr;
     double* t2 = nullptr;
     double* t3 = nullptr;
+    // staging of host-resident states (mfc_rk3_step_batch_host; allocated on first use):
+    // two device states, a dt per state, and the upload / download copy streams
+    double* h[2] = {nullptr, nullptr};
+    double* hdt = nullptr;
+    int32_t hdt_cap = 0;
+    cudaStream_t up = nullptr;
+    cudaStream_t down = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out[2] = {nullptr, nullptr};
     DevScalars* scal = nullptr;
     std::string err;
 };
@@ -441,6 +452,88 @@ mfc_status read_flag(mfc_ctx* ctx, cudaStream_t s) {
     return MFC_OK;
 }
 
+// Device staging for mfc_rk3_step_batch_host: two state buffers, copy
+// streams that do not synchronise with the legacy default stream, and
+// events without timing.  dts holds the dt of every state of one call.
+void release_host_staging(mfc_ctx* ctx) {
+    for (double*& p : ctx->h) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    for (cudaEvent_t* ev : {&ctx->ev_start, &ctx->ev_in[0], &ctx->ev_in[1], &ctx->ev_done[0], &ctx->ev_done[1],
+                            &ctx->ev_out[0], &ctx->ev_out[1]}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
+    for (cudaStream_t* st : {&ctx->up, &ctx->down}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
+    }
+}
+
+mfc_status ensure_host_staging(mfc_ctx* ctx, int32_t count) {
+    const size_t bytes = (size_t)ctx->total * sizeof(double);
+    if (!ctx->h[0]) {
+        bool ok = cudaMalloc(&ctx->h[0], bytes) == cudaSuccess && cudaMalloc(&ctx->h[1], bytes) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->down, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < 2; ++k)
+            ok = cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_out[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            release_host_staging(ctx);
+            return fail(ctx, MFC_ERR_ALLOC, "creating the host staging buffers, streams or events failed");
+        }
+    }
+    if (count > ctx->hdt_cap) {
+        if (ctx->hdt) cudaFree(ctx->hdt);
+        ctx->hdt = nullptr;
+        ctx->hdt_cap = 0;
+        const int32_t cap = count < 64 ? 64 : count;
+        if (cudaMalloc(&ctx->hdt, (size_t)cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, MFC_ERR_ALLOC, "device allocation of the dt array failed");
+        }
+        ctx->hdt_cap = cap;
+    }
+    return MFC_OK;
+}
+
+// Enqueue the pipelined batch (see mfc_rk3_step_batch_host).  State b
+// uses staging buffer b % 2: its upload waits for the download of state
+// b - 2 from the same buffer, its step (on s) waits for the upload, and
+// its download waits for the step.
+mfc_status enqueue_batch_host(mfc_ctx* ctx, int32_t count, const double* const* q_in, double* const* q_out,
+                              double dt, cudaStream_t s) {
+    const size_t bytes = (size_t)ctx->total * sizeof(double);
+    cudaError_t e;
+    if ((e = cudaEventRecord(ctx->ev_start, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->up, ctx->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->down, ctx->ev_start, 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "batch start");
+    for (int32_t b = 0; b < count; ++b) {
+        const int k = b & 1;
+        double* buf = ctx->h[k];
+        if (b >= 2 && (e = cudaStreamWaitEvent(ctx->up, ctx->ev_out[k], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "upload wait");
+        if ((e = cudaMemcpyAsync(buf, q_in[b], bytes, cudaMemcpyHostToDevice, ctx->up)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_in[k], ctx->up)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ctx->ev_in[k], 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "upload");
+        mfc_status st = rk3_once(ctx, buf, dt, ctx->hdt + b, s);
+        if (st != MFC_OK) return st;
+        if ((e = cudaEventRecord(ctx->ev_done[k], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->down, ctx->ev_done[k], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(q_out[b], buf, bytes, cudaMemcpyDeviceToHost, ctx->down)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_out[k], ctx->down)) != cudaSuccess)
+            return cuda_fail(ctx, e, "download");
+    }
+    return MFC_OK;
+}
+
 #define MFC_CHECK_CTX(ctx)                  \
     do {                                    \
         if (!(ctx)) return MFC_ERR_ARG;     \
@@ -507,8 +600,9 @@ mfc_status mfc_destroy(mfc_ctx* ctx) {
     if (!ctx) return MFC_OK;
     DeviceGuard guard(ctx->device);
     cudaDeviceSynchronize();
-    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3, ctx->t1, ctx->t2, ctx->t3})
+    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3, ctx->t1, ctx->t2, ctx->t3, ctx->hdt})
         if (p) cudaFree(p);
+    release_host_staging(ctx);
     if (ctx->scal) cudaFree(ctx->scal);
     delete ctx;
     return MFC_OK;
@@ -572,6 +666,36 @@ mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, doubl
         if (st != MFC_OK) return st;
     }
     return MFC_OK;
+}
+
+mfc_status mfc_rk3_step_batch_host(mfc_ctx* ctx, int32_t count, const double* const* q_in, double* const* q_out,
+                                   double dt, double* dt_used, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (count < 0) return fail(ctx, MFC_ERR_ARG, "negative state count");
+    if (count == 0) return MFC_OK;
+    if (!q_in || !q_out) return fail(ctx, MFC_ERR_ARG, "null pointer array");
+    for (int32_t b = 0; b < count; ++b)
+        if (!q_in[b] || !q_out[b]) return fail(ctx, MFC_ERR_ARG, "null host buffer");
+    if (!std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "dt must be finite");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mfc_status st = ensure_host_staging(ctx, count);
+    if (st != MFC_OK) return st;
+    st = enqueue_batch_host(ctx, count, q_in, q_out, dt, s);
+    // drain all three streams whatever happened, so that no copy into or
+    // out of the caller's host buffers is in flight after the return
+    cudaError_t e1 = cudaStreamSynchronize(ctx->up);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->down);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    if (st != MFC_OK) return st;
+    if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "upload stream");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "download stream");
+    if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "step stream");
+    if (dt_used) {
+        cudaError_t e = cudaMemcpy(dt_used, ctx->hdt, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dt read-back");
+    }
+    return read_flag(ctx, s);
 }
 
 mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, double* q_bar, void* stream) {

@@ -73,6 +73,8 @@ _SIGS = {
     "mfc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mfc_rk3_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _VP]),
     "mfc_rk3_run": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_double, _VP, _VP]),
+    "mfc_rk3_step_batch_host": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                               ctypes.c_double, _VP, _VP]),
     "mfc_rhs_vjp": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "mfc_rk3_step_vjp": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _VP, _VP]),
     "mfc_check": (ctypes.c_int, [_VP, _VP]),
@@ -150,6 +152,14 @@ def mfc_rk3_step(ctx, q, dt, dt_used, stream) -> None:
 
 def mfc_rk3_run(ctx, q, nsteps, dt, dt_log, stream) -> None:
     _err(ctx, lib().mfc_rk3_run(ctx, q, int(nsteps), float(dt), dt_log, stream))
+
+
+def mfc_rk3_step_batch_host(ctx, count, q_in, q_out, dt, dt_used, stream) -> None:
+    """q_in, q_out: sequences of `count` host addresses (ints); dt_used: a host
+    address of `count` doubles or None."""
+    ins = (_VP * max(int(count), 1))(*q_in)
+    outs = (_VP * max(int(count), 1))(*q_out)
+    _err(ctx, lib().mfc_rk3_step_batch_host(ctx, int(count), ins, outs, float(dt), dt_used, stream))
 
 
 def mfc_rhs_vjp(ctx, q, rhs_bar, q_bar, stream) -> None:
@@ -302,6 +312,21 @@ class Solver:
             assert dt_log.dtype == torch.float64 and dt_log.is_cuda and dt_log.numel() >= nsteps
         mfc_rk3_run(self.ctx, _ptr(q), nsteps, dt, _ptr(dt_log), self._stream())
         return q
+
+    def rk3_step_batch_host(self, q_in, q_out, dt: float = 0.0) -> torch.Tensor:
+        """One RK3 step of each host state q_in[b] into q_out[b] (CPU float64
+        tensors of the state shape; pinned ones let the copies overlap the
+        steps).  Returns the dt each state took (a CPU tensor)."""
+        if len(q_in) != len(q_out):
+            raise ValueError("q_in and q_out must have the same length")
+        for t in (*q_in, *q_out):
+            if t.dtype != torch.float64 or t.device.type != "cpu" or not t.is_contiguous() \
+                    or tuple(t.shape) != self.shape:
+                raise ValueError(f"expected contiguous float64 CPU tensors of shape {self.shape}")
+        dts = torch.zeros(max(len(q_in), 1), dtype=torch.float64)
+        mfc_rk3_step_batch_host(self.ctx, len(q_in), [t.data_ptr() for t in q_in], [t.data_ptr() for t in q_out],
+                                dt, dts.data_ptr(), self._stream())
+        return dts[:len(q_in)]
 
     def rhs_vjp(self, q: torch.Tensor, rhs_bar: torch.Tensor, q_bar: Optional[torch.Tensor] = None) -> torch.Tensor:
         q_bar = self.empty() if q_bar is None else q_bar
