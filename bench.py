@@ -271,9 +271,12 @@ PREC = {"fp64": 0, "mixed": 1, "fp64_fast": 2}
 
 
 def time_vjp(S, q, dt: float, reps: int) -> float:
-    """Milliseconds per mfc_rk3_step_vjp (stage recomputation included)."""
-    g = S.empty()
-    g.copy_(q)
+    """Milliseconds per mfc_rk3_step_vjp (stage recomputation included).
+    The cotangent is seeded standard-normal noise, a generic objective's
+    gradient.  (An all-ones cotangent is degenerate: its flux differences
+    vanish, and the kernels skip the zero bars.)"""
+    gen = torch.Generator(device=q.device).manual_seed(1)
+    g = torch.randn(q.shape, generator=gen, dtype=torch.float64, device=q.device)
     out = S.empty()
     stream = torch.cuda.current_stream()
     S.rk3_step_vjp(q, dt, g, out)

@@ -54,6 +54,7 @@ class _Problem(ctypes.Structure):
         ("gamma", ctypes.c_double * MAXF), ("pi_inf", ctypes.c_double * MAXF),
         ("weno", ctypes.c_int32), ("eps", ctypes.c_double), ("teno_ct", ctypes.c_double),
         ("model", ctypes.c_int32), ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32),
+        ("eta", ctypes.c_double * MAXF),
     ]
 
 
@@ -71,6 +72,7 @@ def _load():
                 "oc_cons_to_prim": (ctypes.c_int, [P, dp, dp]),
                 "oc_dt": (ctypes.c_double, [P, dp, ctypes.c_double]),
                 "oc_rhs": (ctypes.c_int, [P, dp, dp]),
+                "oc_viscous_rhs": (ctypes.c_int, [P, dp, dp]),
                 "oc_rk3_step": (ctypes.c_int, [P, dp, ctypes.c_double]),
                 "oc_rk3_run": (ctypes.c_int, [P, dp, ctypes.c_int, ctypes.c_double, dp, dp]),
                 "oc_rhs_jvp": (ctypes.c_int, [P, dp, dp, dp, dp]),
@@ -106,6 +108,7 @@ class Problem:
     model: int = 0                        # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
     riemann: int = 0                      # 0: HLLC; 1: HLL
     low_mach: int = 0                     # 0: none; 1: Thornber; 2: anti-dissipation pressure correction
+    eta: Sequence[float] = None           # shear viscosity per fluid; None or zeros: inviscid
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -142,6 +145,7 @@ class Problem:
         for i in range(MAXF):
             p.gamma[i] = float(self.gamma[i]) if i < self.nf else 0.0
             p.pi_inf[i] = float(self.pi_inf[i]) if i < self.nf else 0.0
+            p.eta[i] = float(self.eta[i]) if (self.eta is not None and i < self.nf) else 0.0
         p.weno, p.eps, p.teno_ct = int(self.weno), float(self.eps), float(self.teno_ct)
         p.model, p.riemann, p.low_mach = int(self.model), int(self.riemann), int(self.low_mach)
         return p
@@ -193,6 +197,13 @@ def rhs(P: Problem, q, return_bad: bool = False):
     lib = _load(); c = P.cstruct(); q = _arr(P, q); L = np.empty_like(q)
     bad = _check(lib.oc_rhs(ctypes.byref(c), _dp(q), _dp(L)), "rhs")
     return (L, bad) if return_bad else L
+
+
+def viscous_rhs(P: Problem, q) -> np.ndarray:
+    """The viscous part of L(q) alone."""
+    lib = _load(); c = P.cstruct(); q = _arr(P, q); V = np.empty_like(q)
+    _check(lib.oc_viscous_rhs(ctypes.byref(c), _dp(q), _dp(V)), "viscous_rhs")
+    return V
 
 
 def rk3_step(P: Problem, q, dt: float, return_bad: bool = False):

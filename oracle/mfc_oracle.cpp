@@ -30,6 +30,8 @@
  *   * HLLC and HLL approximate Riemann solvers, Sec. 3.2.2 (Toro), with the
  *     low-Mach corrections of Sec. 4.2.4 (Thornber's velocity modification,
  *     Chen's anti-dissipation pressure correction for HLLC);
+ *   * the viscous stress T^v = 2 eta (D - tr(D) I/3) of Sec. 2.1.1 in the
+ *     momentum and energy fluxes (optional: all eta_i = 0 is inviscid);
  *   * ghost cells by periodic wrap, zeroth-order extrapolation or mirror
  *     with negated normal momentum, Sec. 3.3;
  *   * third-order TVD Runge-Kutta, Sec. 3.4 (the same tableau as the
@@ -78,6 +80,7 @@ typedef struct {
     int32_t model;    /* 0: K = 0 (Allaire); 1: Kapila K div u, two fluids */
     int32_t riemann;  /* 0: HLLC; 1: HLL */
     int32_t low_mach; /* 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC) */
+    double eta[MAXF]; /* shear viscosity of each fluid; all zero: inviscid */
 } oc_problem;
 }
 
@@ -169,13 +172,17 @@ struct Lay {
 struct Eos {
     int nf;
     int model, riemann, low_mach;
-    double g[MAXF], h[MAXF], gam[MAXF], pinf[MAXF];
-    explicit Eos(const oc_problem& P) : nf(P.nf), model(P.model), riemann(P.riemann), low_mach(P.low_mach) {
+    double g[MAXF], h[MAXF], gam[MAXF], pinf[MAXF], eta[MAXF];
+    bool viscous;
+    explicit Eos(const oc_problem& P)
+        : nf(P.nf), model(P.model), riemann(P.riemann), low_mach(P.low_mach), viscous(false) {
         for (int i = 0; i < nf; ++i) {
             g[i] = 1.0 / (P.gamma[i] - 1.0);
             h[i] = P.gamma[i] * P.pi_inf[i] / (P.gamma[i] - 1.0);
             gam[i] = P.gamma[i];
             pinf[i] = P.pi_inf[i];
+            eta[i] = P.eta[i];
+            if (P.eta[i] > 0.0) viscous = true;
         }
     }
     /* Gamma and Pi from the N_f - 1 stored volume fractions; the last one is
@@ -658,6 +665,97 @@ template <class T> T cell_K(const Lay& L, const Eos& eos, const T* qc) {
     return kapila_K(eos, w[L.E()], w[L.alpha(0)]);
 }
 
+/* ------------------------------------------------------------------ */
+/* Viscous stress (Sec. 2.1.1)                                         */
+/* ------------------------------------------------------------------ */
+
+/* T^v = 2 eta (D - tr(D) I/3) with D = (grad u + (grad u)^T)/2, i.e.
+ *   T_ab = eta (d_a u_b + d_b u_a) - 2/3 eta (div u) delta_ab,
+ * enters the momentum flux as -T and the energy flux as -T.u (Sec. 2.1.1).
+ * Readings (the paper states neither):
+ *   - mixture viscosity eta = sum_i alpha_i eta_i, alpha_N = 1 - sum_j alpha_j;
+ *   - the stress is evaluated on each face by second-order central
+ *     differences of the cell velocities u = (rho u)/rho: on the face
+ *     between cells A = c and B = c + e_ax,
+ *       d_ax u_b = (u_b(B) - u_b(A)) / dx_ax,
+ *       d_t u_b  = ((u_b(A + e_t) - u_b(A - e_t)) + (u_b(B + e_t) - u_b(B - e_t))) / (4 dx_t),  t != ax,
+ *     the face velocity and the face volume fractions being the means of
+ *     A's and B's;
+ *   - ghost cells as for the inviscid flux (a reflective wall mirrors the
+ *     velocity with its normal component negated, i.e. a slip wall).
+ * The viscous right-hand side of a cell sums (G_{c-1/2} - G_{c+1/2})/dx over
+ * the directions in axis order, G being the viscous flux; it is the value
+ * L(q) starts from, the inviscid directional terms being added to it. */
+template <class T, class View>
+void cell_velocity(const View& V, const Lay& L, const int* c, T* q, T* u) {
+    fetch<T>(V, L, c[0], c[1], c[2], q);
+    T rho = q[L.rho(0)];
+    for (int i = 1; i < L.nf; ++i) rho = rho + q[L.rho(i)];
+    for (int d = 0; d < L.nd; ++d) u[d] = q[L.mom(d)] / rho;
+}
+
+template <class T, class View>
+void viscous_face_flux(const View& V, const Lay& L, const Eos& eos, int ax, const int* c, T* G) {
+    const oc_problem& P = *V.P;
+    const int nd = L.nd;
+    int A[3] = {c[0], c[1], c[2]}, B[3] = {c[0], c[1], c[2]};
+    B[ax] += 1;
+    T qA[MAXQ], qB[MAXQ], uA[3], uB[3], tmp[MAXQ];
+    cell_velocity(V, L, A, qA, uA);
+    cell_velocity(V, L, B, qB, uB);
+    T g[3][3];  // g[a][b] = d_a u_b on the face
+    for (int b = 0; b < nd; ++b) g[ax][b] = (uB[b] - uA[b]) / T(dx_of(P, ax));
+    for (int t = 0; t < nd; ++t) {
+        if (t == ax) continue;
+        int Ap[3] = {A[0], A[1], A[2]}, Am[3] = {A[0], A[1], A[2]};
+        int Bp[3] = {B[0], B[1], B[2]}, Bm[3] = {B[0], B[1], B[2]};
+        Ap[t] += 1;
+        Am[t] -= 1;
+        Bp[t] += 1;
+        Bm[t] -= 1;
+        T uAp[3], uAm[3], uBp[3], uBm[3];
+        cell_velocity(V, L, Ap, tmp, uAp);
+        cell_velocity(V, L, Am, tmp, uAm);
+        cell_velocity(V, L, Bp, tmp, uBp);
+        cell_velocity(V, L, Bm, tmp, uBm);
+        for (int b = 0; b < nd; ++b)
+            g[t][b] = ((uAp[b] - uAm[b]) + (uBp[b] - uBm[b])) / T(4.0 * dx_of(P, t));
+    }
+    T div = g[0][0];
+    for (int d = 1; d < nd; ++d) div = div + g[d][d];
+    T s = T(0.0), af[MAXF];
+    for (int j = 0; j < L.nf - 1; ++j) {
+        af[j] = (qA[L.alpha(j)] + qB[L.alpha(j)]) * T(0.5);
+        s = s + af[j];
+    }
+    T eta = (T(1.0) - s) * T(eos.eta[L.nf - 1]);
+    for (int j = 0; j < L.nf - 1; ++j) eta = eta + af[j] * T(eos.eta[j]);
+    for (int k = 0; k < L.nq(); ++k) G[k] = T(0.0);
+    T work = T(0.0);
+    for (int b = 0; b < nd; ++b) {
+        T Tab = eta * (g[ax][b] + g[b][ax]);
+        if (b == ax) Tab = Tab - T(2.0 / 3.0) * eta * div;
+        const T uf = (uA[b] + uB[b]) * T(0.5);
+        work = (b == 0) ? Tab * uf : work + Tab * uf;
+        G[L.mom(b)] = -Tab;
+    }
+    G[L.E()] = -work;
+}
+
+template <class T, class View>
+void viscous_cell(const View& V, const Lay& L, const Eos& eos, const int* c, T* Vc) {
+    const oc_problem& P = *V.P;
+    for (int k = 0; k < L.nq(); ++k) Vc[k] = T(0.0);
+    for (int ax = 0; ax < P.ndim; ++ax) {
+        T Gm[MAXQ], Gp[MAXQ];
+        int cm[3] = {c[0], c[1], c[2]};
+        cm[ax] -= 1;
+        viscous_face_flux(V, L, eos, ax, cm, Gm);
+        viscous_face_flux(V, L, eos, ax, c, Gp);
+        for (int k = 0; k < L.nq(); ++k) Vc[k] = Vc[k] + (Gm[k] - Gp[k]) / T(dx_of(P, ax));
+    }
+}
+
 /* Right-hand side L(q) on every interior cell. */
 template <class T>
 void rhs_full(const oc_problem& P, const T* q, T* Lout) {
@@ -667,6 +765,17 @@ void rhs_full(const oc_problem& P, const T* q, T* Lout) {
     const int64_t ncell = (int64_t)P.n[0] * P.n[1] * P.n[2];
     FullView<T> V{&P, q, ncell};
     for (int64_t i = 0; i < (int64_t)nq * ncell; ++i) Lout[i] = T(0.0);
+    if (eos.viscous) {
+        for (int k = 0; k < P.n[2]; ++k)
+            for (int j = 0; j < P.n[1]; ++j)
+                for (int i = 0; i < P.n[0]; ++i) {
+                    int c[3] = {i, j, k};
+                    T Vc[MAXQ];
+                    viscous_cell(V, L, eos, c, Vc);
+                    const int64_t cl = lin(P, i, j, k);
+                    for (int f = 0; f < nq; ++f) Lout[f * ncell + cl] = Vc[f];
+                }
+    }
     for (int ax = 0; ax < P.ndim; ++ax) {
         const int n = P.n[ax];
         const double dx = dx_of(P, ax);
@@ -702,7 +811,10 @@ void rhs_full(const oc_problem& P, const T* q, T* Lout) {
 template <class T, class View>
 void rhs_cell(const View& V, const Lay& L, const Eos& eos, const int* c, T* Lc) {
     const oc_problem& P = *V.P;
-    for (int k = 0; k < L.nq(); ++k) Lc[k] = T(0.0);
+    if (eos.viscous)
+        viscous_cell(V, L, eos, c, Lc);
+    else
+        for (int k = 0; k < L.nq(); ++k) Lc[k] = T(0.0);
     T qc[MAXQ];
     fetch<T>(V, L, c[0], c[1], c[2], qc);
     T Kc = cell_K(L, eos, qc);
@@ -795,6 +907,8 @@ int check_problem(const oc_problem* P) {
     if (P->model < 0 || P->model > 1 || (P->model == 1 && P->nf != 2)) return -1;
     if (P->riemann < 0 || P->riemann > 1 || P->low_mach < 0 || P->low_mach > 2) return -1;
     if (P->low_mach == 2 && P->riemann != 0) return -1;
+    for (int i = 0; i < P->nf; ++i)
+        if (!(P->eta[i] >= 0.0) || !std::isfinite(P->eta[i])) return -1;
     return 0;
 }
 
@@ -851,6 +965,24 @@ int oc_rhs(const oc_problem* P, const double* q, double* Lout) {
     g_bad = 0;
     rhs_full(*P, q, Lout);
     return g_bad;
+}
+
+/* The viscous part of L(q) alone (zero when every eta_i is 0). */
+int oc_viscous_rhs(const oc_problem* P, const double* q, double* Vout) {
+    if (check_problem(P)) return -1;
+    Lay L{P->nf, P->ndim};
+    Eos eos(*P);
+    const int64_t nc = ncells(P);
+    FullView<double> V{P, q, nc};
+    for (int k = 0; k < P->n[2]; ++k)
+        for (int j = 0; j < P->n[1]; ++j)
+            for (int i = 0; i < P->n[0]; ++i) {
+                int c[3] = {i, j, k};
+                double Vc[MAXQ];
+                viscous_cell(V, L, eos, c, Vc);
+                for (int f = 0; f < L.nq(); ++f) Vout[f * nc + lin(*P, i, j, k)] = Vc[f];
+            }
+    return 0;
 }
 
 /* One RK3 step in place with the given dt. */
@@ -922,6 +1054,8 @@ int oc_rk3_step_sampled(const oc_problem* P, const double* q, double dt, int64_t
         ijk[1] = (int)((c / P->n[0]) % P->n[1]);
         ijk[2] = (int)(c / ((int64_t)P->n[0] * P->n[1]));
     };
+    /* cells the right-hand side of the cells in S reads: +-3 along each
+     * axis, and with viscosity the cells one step along two axes */
     auto closure = [&](const std::unordered_set<int64_t>& S) {
         std::unordered_set<int64_t> R = S;
         for (int64_t c : S) {
@@ -934,6 +1068,17 @@ int oc_rk3_step_sampled(const oc_problem* P, const double* q, double dt, int64_t
                     id[ax] = bc_map(*P, ax, id[ax] + m, fl);
                     R.insert(lin(*P, id[0], id[1], id[2]));
                 }
+            if (eos.viscous)
+                for (int a = 0; a < P->ndim; ++a)
+                    for (int b = a + 1; b < P->ndim; ++b)
+                        for (int sa = -1; sa <= 1; sa += 2)
+                            for (int sb = -1; sb <= 1; sb += 2) {
+                                int id[3] = {ijk[0], ijk[1], ijk[2]};
+                                bool fl = false;
+                                id[a] = bc_map(*P, a, id[a] + sa, fl);
+                                id[b] = bc_map(*P, b, id[b] + sb, fl);
+                                R.insert(lin(*P, id[0], id[1], id[2]));
+                            }
         }
         return R;
     };

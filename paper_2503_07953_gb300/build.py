@@ -49,17 +49,22 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+# The files the forward directional sweep kernels are compiled from.
+SWEEP_SOURCES = ["mfc_device.cuh", "mfc_fwd.cuh", "mfc_launch.h", "mfc_launch_impl.cuh"] + \
+    [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast")]
+
+
 def source_fingerprint() -> str:
-    """Hash of the kernel sources alone (no flags, no machine): identifies
-    the code an ncu capture was taken on."""
+    """Hash of the forward sweep kernels' sources and flags (no machine):
+    identifies the code an ncu capture of those kernels was taken on."""
     h = hashlib.sha256()
-    for d in (CSRC, INCLUDE):
-        for name in sorted(os.listdir(d)):
-            p = os.path.join(d, name)
-            if os.path.isfile(p):
-                h.update(name.encode())
-                with open(p, "rb") as fh:
-                    h.update(fh.read())
+    for name in SWEEP_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    flags = [f for f in ARCH + NVCC_FLAGS if f not in (INCLUDE, CSRC)]  # no machine paths
+    h.update(" ".join(flags).encode())
+    h.update(repr(sorted(PER_SOURCE_FLAGS.items())).encode())
     return h.hexdigest()
 
 

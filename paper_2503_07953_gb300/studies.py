@@ -87,7 +87,10 @@ def sizes(args) -> None:
                    "grind_time_ns": ms * 1e6 / (ncell * case.nq * 3)}
             if args.vjp:
                 dt = S.compute_dt(q)
-                bar = torch.ones_like(q)
+                # seeded noise: an all-ones cotangent would make the flux
+                # differences vanish, and the kernels skip zero bars
+                gen = torch.Generator(device=q.device).manual_seed(1)
+                bar = torch.randn(q.shape, generator=gen, dtype=torch.float64, device=q.device)
                 S.rk3_step_vjp(q, dt, bar)
                 ms_vjp = _timed(lambda: S.rk3_step_vjp(q, dt, bar), 2)
                 rec.update({"ms_per_step_vjp": ms_vjp, "vjp_over_fwd": ms_vjp / ms,

@@ -45,6 +45,7 @@ class Case:
     model: int = 0            # 0: K = 0 (Allaire); 1: Kapila K div u (two fluids)
     riemann: int = 0          # 0: HLLC; 1: HLL
     low_mach: int = 0         # 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC)
+    eta: Optional[List[float]] = None  # shear viscosity per fluid (Sec. 2.1.1); None: inviscid
 
     @property
     def ndim(self) -> int:
@@ -74,11 +75,11 @@ class Case:
 def reduced_units(case: Case, W: np.ndarray, rho0: float, p0: float) -> tuple:
     """The same flow in reduced units: densities over rho0, pressures and
     pi_inf over p0, velocities over u0 = sqrt(p0 / rho0) (lengths unchanged,
-    so times scale by u0).  The Euler equations with the stiffened-gas EOS
-    are invariant under this change of units; the WENO eps, an absolute
-    constant, is not, and in reduced units it sits far above the rounding
-    size of the smoothness indicators of O(1) fields.  Returns a new
-    (case, W)."""
+    so times scale by u0; viscosities over rho0 u0).  The equations with the
+    stiffened-gas EOS are invariant under this change of units; the WENO
+    eps, an absolute constant, is not, and in reduced units it sits far
+    above the rounding size of the smoothness indicators of O(1) fields.
+    Returns a new (case, W)."""
     u0 = math.sqrt(p0 / rho0)
     nf, nd = case.nf, case.ndim
     W = np.array(W, dtype=np.float64, copy=True)
@@ -87,7 +88,8 @@ def reduced_units(case: Case, W: np.ndarray, rho0: float, p0: float) -> tuple:
     W[nf + nd] /= p0
     out = Case(case.name, list(case.n), list(case.lo), list(case.hi), list(case.bc_lo), list(case.bc_hi),
                list(case.gamma), [x / p0 for x in case.pi_inf], case.cfl, case.steps, case.weno, case.eps,
-               case.teno_ct, case.model, case.riemann, case.low_mach)
+               case.teno_ct, case.model, case.riemann, case.low_mach,
+               None if case.eta is None else [x / (rho0 * u0) for x in case.eta])
     return out, W
 
 
@@ -488,3 +490,57 @@ def random_smooth_state(case: Case, seed: int = 0, amp: float = 0.05) -> np.ndar
     vel = [0.3 + amp * fields[2 * nf + d] for d in range(nd)]
     p = 1.0 + amp * fields[2 * nf + nd]
     return _assemble(case, alpha, rho, vel, p)
+
+
+# ---------------------------------------------------------------------------
+# Viscous workloads (the stress of Sec. 2.1.1)
+# ---------------------------------------------------------------------------
+
+def taylor_green(n: int = 256, ndim: int = 3, re: float = 1600.0, mach: float = 0.1, gamma: float = 1.4,
+                 steps: int = 100, dims=None) -> tuple:
+    """Taylor-Green vortex, the paper's viscous example (Sec. 5.3: Re 1600,
+    Ma 0.1).  One fluid (gamma 1.4), the periodic cube [0, 2 pi)^ndim, rho0 = 1,
+    V0 = 1, L = 1, so eta = rho0 V0 L / Re and p0 = rho0 V0^2 / (gamma Ma^2).
+    3D: u = V0 sin x cos y cos z, v = -V0 cos x sin y cos z, w = 0,
+    p = p0 + rho0 V0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2); 2D: u = V0 sin x
+    cos y, v = -V0 cos x sin y, p = p0 + rho0 V0^2 / 4 (cos 2x + cos 2y).
+    Reading (the paper cites the initial condition without printing it): an
+    isothermal start, rho = rho0 p / p0.  CFL 0.4, WENO5-M, HLLC."""
+    if dims is None:
+        dims = [n] * ndim
+    ndim = len(dims)
+    two_pi = 2.0 * math.pi
+    rho0, V0 = 1.0, 1.0
+    p0 = rho0 * V0 ** 2 / (gamma * mach ** 2)
+    case = Case(f"taylor_green_{ndim}d", list(dims), [0.0] * ndim, [two_pi] * ndim, [PERIODIC] * ndim,
+                [PERIODIC] * ndim, [gamma], [0.0], cfl=0.4, steps=steps, eta=[rho0 * V0 / re])
+    X, Y, Z = _centres(case)
+    if ndim == 3:
+        u = V0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+        v = -V0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+        w = np.zeros_like(u)
+        p = p0 + rho0 * V0 ** 2 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+        vel = [u, v, w]
+    else:
+        u = V0 * np.sin(X) * np.cos(Y)
+        v = -V0 * np.cos(X) * np.sin(Y)
+        p = p0 + rho0 * V0 ** 2 / 4.0 * (np.cos(2 * X) + np.cos(2 * Y))
+        vel = [u, v]
+    rho = rho0 * p / p0
+    W = _assemble(case, [np.ones_like(rho)], [rho], vel, p)
+    return case, W
+
+
+def shear_wave_2d(n: int = 32, amp: float = 1e-3, eta: float = 0.02, p0: float = 100.0, gamma: float = 1.4,
+                  k: int = 1) -> tuple:
+    """A decaying shear wave: v = amp sin(2 pi k x), u = 0, rho = 1, p = p0 on
+    the periodic unit square, one fluid of viscosity eta.  It is an exact
+    solution of the compressible Navier-Stokes equations up to the viscous
+    heating, of relative size amp^2: v decays as exp(-eta (2 pi k)^2 t / rho),
+    with no pressure or density change."""
+    case = Case("shear_wave_2d", [n, 4], [0.0, 0.0], [1.0, 4.0 / n], [PERIODIC] * 2, [PERIODIC] * 2,
+                [gamma], [0.0], cfl=0.4, steps=0, eta=[eta])
+    X, Y, _ = _centres(case)
+    v = amp * np.sin(2.0 * math.pi * k * X) + 0.0 * Y
+    W = _assemble(case, [np.ones_like(v)], [np.ones_like(v)], [np.zeros_like(v), v], np.full_like(v, p0))
+    return case, W
