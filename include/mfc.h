@@ -100,11 +100,24 @@ typedef struct {
     int32_t bc_lo[3], bc_hi[3];  /* mfc_bc */
 } mfc_grid;
 
-/* Stiffened-gas fluids (Sec. 2.2): gamma_i > 1, pi_inf_i >= 0. */
+/* Stiffened-gas fluids (Sec. 2.2): gamma_i > 1, pi_inf_i >= 0.
+ * eta_i >= 0: shear viscosity of fluid i.  When some eta_i > 0 the fluxes
+ * carry the viscous stress of Sec. 2.1.1, T = 2 eta (D - tr(D) I/3) with
+ * D = (grad u + (grad u)^T)/2 (momentum flux -T, energy flux -T.u), the
+ * mixture viscosity being eta = sum_i alpha_i eta_i.  The stress is taken on
+ * each face by second-order central differences of the cell velocities
+ * (normal derivative across the face; tangential derivatives the mean of
+ * the two cells' centred differences; face velocity and volume fractions
+ * the means of the two cells').  The CFL dt stays the convective one: the
+ * explicit viscous limit rho dx^2 / (2 ndim eta) is the caller's to respect
+ * (pass dt > 0).  With viscosity the adjoints and mfc_rk3_step_noalloc
+ * return MFC_ERR_UNSUPPORTED.  All eta_i = 0 is the inviscid method, bit
+ * for bit. */
 typedef struct {
     int32_t nfluids;       /* 1 .. 4 */
     double gamma[4];
     double pi_inf[4];
+    double eta[4];
 } mfc_eos;
 
 /* Volume-fraction equation (Sec. 2.1.1): alpha_t + u . grad alpha = K div u.

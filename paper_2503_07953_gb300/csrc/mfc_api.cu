@@ -47,6 +47,8 @@ struct mfc_ctx {
     double* t1 = nullptr;
     double* t2 = nullptr;
     double* t3 = nullptr;
+    // cell velocities for the viscous stress (allocated at init when some eta_i > 0)
+    double* vel = nullptr;
     // staging of host-resident states (mfc_rk3_step_batch_host; allocated on first use):
     // two device states, a dt per state, and the upload / download copy streams
     double* h[2] = {nullptr, nullptr};
@@ -188,6 +190,7 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
     for (int i = 0; i < e->nfluids; ++i) {
         if (!(e->gamma[i] > 1.0) || !std::isfinite(e->gamma[i])) return "gamma must be > 1";
         if (!(e->pi_inf[i] >= 0.0) || !std::isfinite(e->pi_inf[i])) return "pi_inf must be >= 0";
+        if (!(e->eta[i] >= 0.0) || !std::isfinite(e->eta[i])) return "eta must be >= 0";
     }
     if (o->precision != MFC_FP64 && o->precision != MFC_MIXED && o->precision != MFC_FP64_FAST)
         return "unknown precision";
@@ -251,6 +254,12 @@ void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Co
         C.gamf[i] = (float)C.gam[i];
         C.pinff[i] = (float)C.pinf[i];
     }
+    C.viscous = 0;
+    for (int i = 0; i < 4; ++i) {
+        C.eta[i] = i < e->nfluids ? e->eta[i] : 0.0;
+        C.etaf[i] = (float)C.eta[i];
+        if (C.eta[i] > 0.0) C.viscous = 1;
+    }
     C.cfl = o->cfl;
     total = C.fstride * C.nq;
 }
@@ -286,22 +295,30 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
     return MFC_OK;
 }
 
-// All directional sweeps of one evaluation of L(qin).  out_kind 0 writes
-// L into rhs; 1 and 2 fuse the RK stage update into the last sweep.  The
+// All directional sweeps of one evaluation of L(qin), after the viscous
+// kernels when some eta_i > 0 (their result is the starting value of the
+// accumulation).  out_kind 0 writes L into rhs; 1 and 2 fuse the RK stage
+// update into the last sweep.  The
 // mixed mode sums the directions in a float accumulator that aliases the
 // scratch buffer ctx->r (first half; rhs may be ctx->r itself only when
 // out_kind is 1 or 2, where rhs is not written).
 mfc_status eval_L(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, const double* qn, double* qout,
                   double a, double b, cudaStream_t s) {
     const bool mixed = ctx->mode == mfc::MODE_MIXED;
+    float* accf = reinterpret_cast<float*>(ctx->r);
+    if (ctx->C.viscous) {
+        // the viscous right-hand side is the value the sweeps accumulate onto
+        cudaError_t e = ctx->fns->viscous(ctx->C, ctx->mode, qin, ctx->vel, rhs, accf, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "viscous kernels");
+    }
     for (int d = 0; d < ctx->C.nd; ++d) {
         mfc::SweepArgs A;
         std::memset(&A, 0, sizeof(A));
         A.q = qin;
         A.rhs = rhs;
-        A.rhsf = reinterpret_cast<float*>(ctx->r);
+        A.rhsf = accf;
         const bool last = d == ctx->C.nd - 1;
-        A.acc_in = d == 0 ? 0 : (mixed ? 2 : 1);
+        A.acc_in = (d == 0 && !ctx->C.viscous) ? 0 : (mixed ? 2 : 1);
         A.out_kind = last ? out_kind : (mixed ? 3 : 0);
         A.qn = qn;
         A.qout = qout;
@@ -585,6 +602,12 @@ mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* op
         mfc_destroy(ctx);
         return MFC_ERR_ALLOC;
     }
+    if (ctx->C.viscous && cudaMalloc(&ctx->vel, (size_t)ctx->C.nd * ctx->C.fstride * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        g_init_error = "device allocation of the velocity scratch failed";
+        mfc_destroy(ctx);
+        return MFC_ERR_ALLOC;
+    }
     if ((e = cudaMemset(ctx->scal, 0, sizeof(DevScalars))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         g_init_error = std::string("initialising scalars: ") + cudaGetErrorString(e);
@@ -600,7 +623,8 @@ mfc_status mfc_destroy(mfc_ctx* ctx) {
     if (!ctx) return MFC_OK;
     DeviceGuard guard(ctx->device);
     cudaDeviceSynchronize();
-    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3, ctx->t1, ctx->t2, ctx->t3, ctx->hdt})
+    for (double* p : {ctx->q1, ctx->q2, ctx->r, ctx->a1, ctx->a2, ctx->a3, ctx->t1, ctx->t2, ctx->t3, ctx->hdt,
+                      ctx->vel})
         if (p) cudaFree(p);
     release_host_staging(ctx);
     if (ctx->scal) cudaFree(ctx->scal);
@@ -702,6 +726,7 @@ mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, dou
     MFC_CHECK_CTX(ctx);
     if (!q || !rhs_bar || !q_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
     if (q_bar == q || q_bar == rhs_bar) return fail(ctx, MFC_ERR_ARG, "q_bar must not alias q or rhs_bar");
+    if (ctx->C.viscous) return fail(ctx, MFC_ERR_UNSUPPORTED, "the adjoint of the viscous term is not implemented");
     DeviceGuard guard(ctx->device);
     return eval_L_vjp(ctx, q, rhs_bar, q_bar, (cudaStream_t)stream);
 }
@@ -712,6 +737,7 @@ mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const do
     if (!q_n || !qnp1_bar || !qn_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "the adjoint needs the step's dt > 0");
     if (qn_bar == q_n || qnp1_bar == q_n) return fail(ctx, MFC_ERR_ARG, "bars must not alias q_n");
+    if (ctx->C.viscous) return fail(ctx, MFC_ERR_UNSUPPORTED, "the adjoint of the viscous term is not implemented");
     DeviceGuard guard(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     mfc_status st = ensure_adjoint_scratch(ctx);
@@ -778,6 +804,10 @@ extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* 
     }
     mfc_ctx ctx;
     make_consts(grid, eos, opts, ctx.C, ctx.total);
+    if (ctx.C.viscous) {
+        g_init_error = "the allocation-free step has no scratch for the viscous stress";
+        return MFC_ERR_UNSUPPORTED;
+    }
     if (kNoallocScalarDoubles + 3 * ctx.total > (int64_t)MFC_NOALLOC_SCRATCH_DOUBLES) {
         g_init_error = "state too large for the allocation-free step: 3 x (padded cells x fields) + 32 must not "
                        "exceed MFC_NOALLOC_SCRATCH_DOUBLES";

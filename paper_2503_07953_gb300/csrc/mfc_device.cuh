@@ -51,6 +51,9 @@ struct Consts {
     int low_mach;             // 0: none; 1: Thornber; 2: anti-dissipation pressure correction
     double gam[2], pinf[2];   // phasic gamma_i, pi_i of the two fluids (Kapila)
     float gamf[2], pinff[2];
+    int viscous;              // 1 when some eta_i > 0 (Sec. 2.1.1 viscous stress)
+    double eta[MAXF];         // phasic shear viscosities
+    float etaf[MAXF];
     double cfl;
 };
 

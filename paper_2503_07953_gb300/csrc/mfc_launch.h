@@ -52,6 +52,11 @@ struct LaunchFns {
     // CFL minimum of dx_d / (|u_d| + c) into *minbits (atomicMin), in the
     // table's float64 arithmetic.
     cudaError_t (*cfl)(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s);
+    // Viscous stress (mfc_visc.cuh): the cell velocities of q into vel
+    // (ND fields of the mode's precision in the padded layout), then the
+    // viscous right-hand side into rhs (float64) or rhsf (MODE_MIXED).
+    cudaError_t (*viscous)(const Consts& C, int mode, const double* q, void* vel, double* rhs, float* rhsf,
+                           cudaStream_t s);
     // Exact tables only: the primitive / conservative maps.
     cudaError_t (*prim_to_cons)(const Consts& C, const double* w, double* q, cudaStream_t s);
     cudaError_t (*cons_to_prim)(const Consts& C, const double* q, double* w, int* flag, cudaStream_t s);

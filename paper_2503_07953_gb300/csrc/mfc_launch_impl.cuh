@@ -7,6 +7,7 @@
 
 #include "mfc_fwd.cuh"
 #include "mfc_launch.h"
+#include "mfc_visc.cuh"
 #include "mfc_vjp.cuh"
 
 namespace mfc {
@@ -132,6 +133,15 @@ cudaError_t sweep_vjp_nd(const Consts& C, int dir, int mode, VjpArgs A, cudaStre
     return cudaGetLastError();
 }
 
+template <int NF, int ND, int MODE>
+cudaError_t viscous_nd(const Consts& C, const double* q, void* vel, double* rhs, float* rhsf, cudaStream_t s) {
+    using R = typename ModeT<MODE>::R;
+    const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
+    velocity_kernel<NF, ND, MODE><<<stride_grid(ncell, 256), 256, 0, s>>>(C, q, static_cast<R*>(vel));
+    viscous_kernel<NF, ND, MODE><<<grid_for(ncell, 128), 128, 0, s>>>(C, q, static_cast<const R*>(vel), rhs, rhsf);
+    return cudaGetLastError();
+}
+
 template <int NF, bool EXACT>
 struct Launch {
     static cudaError_t sweep(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s) {
@@ -147,6 +157,20 @@ struct Launch {
             case 2: return sweep_vjp_nd<NF, 2, EXACT>(C, dir, mode, A, s);
             default: return sweep_vjp_nd<NF, 3, EXACT>(C, dir, mode, A, s);
         }
+    }
+    static cudaError_t viscous(const Consts& C, int mode, const double* q, void* vel, double* rhs, float* rhsf,
+                               cudaStream_t s) {
+        auto go = [&](auto modec) -> cudaError_t {
+            constexpr int M = decltype(modec)::value;
+            switch (C.nd) {
+                case 1: return viscous_nd<NF, 1, M>(C, q, vel, rhs, rhsf, s);
+                case 2: return viscous_nd<NF, 2, M>(C, q, vel, rhs, rhsf, s);
+                default: return viscous_nd<NF, 3, M>(C, q, vel, rhs, rhsf, s);
+            }
+        };
+        if constexpr (EXACT) return go(std::integral_constant<int, MODE_EXACT>());
+        else if (mode == MODE_MIXED) return go(std::integral_constant<int, MODE_MIXED>());
+        else return go(std::integral_constant<int, MODE_FAST>());
     }
     static cudaError_t cfl(const Consts& C, const double* q, unsigned long long* minbits, int* flag, cudaStream_t s) {
         const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
@@ -187,7 +211,8 @@ struct Launch {
         return cudaGetLastError();
     }
     static const LaunchFns& fns() {
-        static const LaunchFns f = {&sweep, &sweep_vjp, &cfl, EXACT ? &p2c : nullptr, EXACT ? &c2p : nullptr};
+        static const LaunchFns f = {&sweep, &sweep_vjp, &cfl, &viscous, EXACT ? &p2c : nullptr,
+                                    EXACT ? &c2p : nullptr};
         return f;
     }
 };

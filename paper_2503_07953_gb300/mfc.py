@@ -48,7 +48,8 @@ class mfc_grid(ctypes.Structure):
 
 
 class mfc_eos(ctypes.Structure):
-    _fields_ = [("nfluids", ctypes.c_int32), ("gamma", ctypes.c_double * 4), ("pi_inf", ctypes.c_double * 4)]
+    _fields_ = [("nfluids", ctypes.c_int32), ("gamma", ctypes.c_double * 4), ("pi_inf", ctypes.c_double * 4),
+                ("eta", ctypes.c_double * 4)]
 
 
 class mfc_opts(ctypes.Structure):
@@ -200,7 +201,7 @@ class Solver:
                  ghost: int = 3, precision: int = MFC_FP64, weno: int = MFC_WENO_M,
                  weno_eps: Optional[float] = None, cfl: float = 0.4, teno_ct: float = 1e-6,
                  model: int = MFC_MODEL_K0, riemann: int = MFC_RIEMANN_HLLC,
-                 low_mach: int = MFC_LOW_MACH_NONE, device=None):
+                 low_mach: int = MFC_LOW_MACH_NONE, eta: Optional[Sequence[float]] = None, device=None):
         nd = len(n)
         self.ndim, self.nf = nd, len(gamma)
         self.n = [int(x) for x in n] + [1] * (3 - nd)
@@ -221,6 +222,7 @@ class Solver:
         for i in range(min(4, self.nf)):
             e.gamma[i] = float(gamma[i])
             e.pi_inf[i] = float(pi_inf[i])
+            e.eta[i] = float(eta[i]) if eta is not None else 0.0
         o = mfc_opts()
         o.precision = self.precision
         o.weno = int(weno)
@@ -242,7 +244,8 @@ class Solver:
     def from_case(cls, case, **kw):
         return cls(case.n, case.gamma, case.pi_inf, lo=case.lo, hi=case.hi, bc_lo=case.bc_lo,
                    bc_hi=case.bc_hi, weno=case.weno, weno_eps=case.eps, cfl=case.cfl, teno_ct=case.teno_ct,
-                   model=case.model, riemann=case.riemann, low_mach=case.low_mach, **kw)
+                   model=case.model, riemann=case.riemann, low_mach=case.low_mach,
+                   eta=getattr(case, "eta", None), **kw)
 
     # layout helpers
     def empty(self) -> torch.Tensor:

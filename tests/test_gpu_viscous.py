@@ -1,0 +1,193 @@
+"""Parity of the CUDA viscous stress (Sec. 2.1.1) with the oracle: the
+right-hand side and RK3 runs bit for bit in MFC_FP64, within 1e-11 per field
+in MFC_FP64_FAST and 1e-4 in MFC_MIXED (float32 stress; 5e-3 for the
+right-hand side of the low-Mach Taylor-Green vortex), on the Taylor-Green
+vortex (one fluid, periodic) and on multi-fluid states with reflective and
+transmissive walls (corner ghost cells).  Also the full-size 256^3
+Taylor-Green step at sampled cells, the discrete shear-wave decay rate, and
+the refusals of the unsupported combinations."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_07953_gb300 import workloads as wl
+from tests.helpers import case_errors, oracle_problem, solver_for, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def walled_case(dims, nf, seed=0):
+    """A smooth multi-fluid state, reflective walls on x, transmissive on the
+    other axes, every fluid viscous."""
+    nd = len(dims)
+    bl = [wl.REFLECTIVE] + [wl.TRANSMISSIVE] * (nd - 1)
+    bh = [wl.REFLECTIVE] + [wl.TRANSMISSIVE] * (nd - 1)
+    case = wl.Case("walled", list(dims), [0.0] * nd, [1.0] * nd, bl, bh, [1.4, 1.67, 4.4][:nf],
+                   [0.0, 0.0, 6.0][:nf], 0.4, 0, eta=[0.02, 0.005, 0.04][:nf])
+    X, Y, Z = wl._centres(case)
+    tp = 2.0 * math.pi
+    r = np.random.default_rng(seed).uniform(0.5, 1.0, size=6)
+    one = np.ones(case.shape[1:])
+    vel = [0.3 * r[d] * np.sin(tp * (X + r[3] * Y + r[4] * Z) + d) * one for d in range(nd)]
+    p = (10.0 + np.cos(tp * (X - Y + 0.5 * Z))) * one
+    a1 = (0.4 + 0.3 * np.sin(tp * (X + Z))) * one
+    alpha = [a1, 1.0 - a1] if nf == 2 else [a1, 0.5 * (1.0 - a1), 0.5 * (1.0 - a1)]
+    rho_ph = [(1.0 + 0.2 * np.cos(tp * Y)) * one, 0.5 * one, 2.0 * one][:nf]
+    W = wl._assemble(case, alpha[:nf], rho_ph, vel, p)
+    return case, W
+
+
+CASES = {
+    "taylor_green_3d": lambda: wl.taylor_green(dims=[12, 10, 8], re=200.0),
+    "taylor_green_2d": lambda: wl.taylor_green(dims=[16, 12], re=100.0),
+    "walled_2d_nf2": lambda: walled_case([14, 11], 2),
+    "walled_3d_nf3": lambda: walled_case([9, 8, 7], 3),
+    "walled_1d_nf2": lambda: walled_case([40], 2),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_bitwise(oracle_lib, mfc_lib, cuda_device, name):
+    case, W = CASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    L_o, bad = oracle_lib.rhs(P, q_o, return_bad=True)
+    assert bad == 0
+    got = to_host(S, S.rhs(S.from_interior(q_o)))
+    assert np.array_equal(got, L_o), case_errors(case, got, L_o)
+    # the viscous part is a real contribution, not a rounding-level one
+    V = oracle_lib.viscous_rhs(P, q_o)
+    k = case.nf
+    assert np.abs(V[k]).max() > 1e-3 * np.abs(L_o[k]).max()
+
+
+# MFC_MIXED on the Taylor-Green vortex: at Ma 0.1 the divergence of the
+# fluxes is a small difference of large ones (the pressure is 71 around
+# variations of 0.06, the energy flux (E + p) u ~ 250 around a divergence of
+# ~0.3), so float32 fluxes carry about 1e-3 of L (measured: <= 1.9e-3).
+MIXED_LOW_MACH_TOL = 5e-3
+
+
+@pytest.mark.parametrize("prec,tol", [(2, TOL), (1, 1e-4)])
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_fast_and_mixed(oracle_lib, mfc_lib, cuda_device, name, prec, tol):
+    if prec == 1 and name.startswith("taylor_green"):
+        tol = MIXED_LOW_MACH_TOL
+    case, W = CASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    got = to_host(S, S.rhs(S.from_interior(q_o)))
+    L_o = oracle_lib.rhs(P, q_o)
+    err = case_errors(case, got, L_o)
+    assert (err <= tol).all(), err
+
+
+@pytest.mark.parametrize("name", ["taylor_green_3d", "walled_2d_nf2", "walled_3d_nf3"])
+def test_rk3_run_bitwise(oracle_lib, mfc_lib, cuda_device, name):
+    case, W = CASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    q_g = S.from_interior(q_o)
+    dt_log = torch.zeros(20, dtype=torch.float64, device=cuda_device)
+    S.rk3_run(q_g, 20, 0.0, dt_log)
+    S.check()
+    q_end, dts = oracle_lib.rk3_run(P, q_o, 20, cfl=case.cfl)
+    assert np.array_equal(dt_log.cpu().numpy(), dts)
+    got = to_host(S, q_g)
+    assert np.array_equal(got, q_end), case_errors(case, got, q_end)
+
+
+@pytest.mark.parametrize("prec,tol", [(2, TOL), (1, 1e-4)])
+def test_rk3_run_fast_and_mixed(oracle_lib, mfc_lib, cuda_device, prec, tol):
+    case, W = CASES["walled_3d_nf3"]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    q_end, dts = oracle_lib.rk3_run(P, q_o, 20, cfl=case.cfl)
+    q_g = S.from_interior(q_o)
+    for dt in dts:
+        S.rk3_step(q_g, float(dt))
+    S.check()
+    err = case_errors(case, to_host(S, q_g), q_end)
+    assert (err <= tol).all(), err
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_full_size_taylor_green_step_sampled(oracle_lib, mfc_lib, cuda_device, prec):
+    """The 256^3 Taylor-Green vortex (Re 1600, Ma 0.1): one step on the GPU,
+    checked at sampled cells (including the periodic corners) against the
+    oracle's domain-of-dependence evaluation of the same step."""
+    case, W = wl.taylor_green(256)
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=prec)
+    q_g = S.prim_to_cons(S.from_interior(W))
+    q_o = to_host(S, q_g)
+    dt = oracle_lib.cfl_dt(P, q_o, case.cfl)
+    S.rk3_step(q_g, dt)
+    S.check()
+    out_g = to_host(S, q_g)
+    rng = np.random.default_rng(1)
+    cells = [(0, 0, 0), (255, 255, 255), (0, 255, 128), (255, 0, 3), (64, 64, 64), (128, 1, 254)]
+    cells += [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(6)]
+    ref = oracle_lib.rk3_step_sampled(P, q_o, dt, cells)
+    got = np.stack([out_g[:, k, j, i] for (i, j, k) in cells])
+    if prec == mfc_lib.MFC_FP64:
+        assert np.array_equal(got, ref)
+    else:
+        scale = np.abs(out_g).max(axis=(1, 2, 3))
+        scale[case.nf:case.nf + case.ndim] = scale[case.nf:case.nf + case.ndim].max()
+        err = (np.abs(got - ref) / scale).max(axis=0)
+        assert (err <= (TOL if prec == mfc_lib.MFC_FP64_FAST else 1e-5)).all(), err
+
+
+def test_shear_wave_decay_rate(mfc_lib, cuda_device):
+    """MFC_FP64_FAST, 128 cells per wavelength: the decay rate of the
+    discrete Laplacian's eigenvalue, eta 2 (1 - cos(2 pi h)) / h^2."""
+    case, W = wl.shear_wave_2d(128)
+    S = solver_for(mfc_lib, case, precision=2)
+    q = S.prim_to_cons(S.from_interior(W))
+    X, Y, _ = wl._centres(case)
+    mode = torch.as_tensor(np.sin(2.0 * math.pi * X) + 0.0 * Y, device=cuda_device)
+
+    def amplitude(q):
+        qi = S.interior(q)
+        return float(2.0 * ((qi[2] / qi[0])[0] * mode).mean())
+
+    a0 = amplitude(q)
+    dt_log = torch.zeros(400, dtype=torch.float64, device=cuda_device)
+    S.rk3_run(q, 400, 0.0, dt_log)
+    S.check()
+    rate = -math.log(amplitude(q) / a0) / float(dt_log.sum())
+    eta, h = case.eta[0], 1.0 / 128
+    assert rate == pytest.approx(eta * 2.0 * (1.0 - math.cos(2.0 * math.pi * h)) / h ** 2, rel=1e-7)
+
+
+def test_inviscid_unchanged_and_refusals(oracle_lib, mfc_lib, cuda_device):
+    case, W = CASES["walled_2d_nf2"]()
+    q_o = oracle_lib.prim_to_cons(oracle_problem(oracle_lib, case), W)
+    visc = case.eta
+    case.eta = [0.0, 0.0]
+    Sz = solver_for(mfc_lib, case)
+    case.eta = None
+    Sn = solver_for(mfc_lib, case)
+    assert np.array_equal(to_host(Sz, Sz.rhs(Sz.from_interior(q_o))), to_host(Sn, Sn.rhs(Sn.from_interior(q_o))))
+    case.eta = visc
+    S = solver_for(mfc_lib, case)
+    q = S.from_interior(q_o)
+    with pytest.raises(mfc_lib.MfcError) as ei:
+        S.rhs_vjp(q, torch.ones_like(q))
+    assert ei.value.status == mfc_lib.MFC_ERR_UNSUPPORTED
+    with pytest.raises(mfc_lib.MfcError) as ei:
+        S.rk3_step_vjp(q, 1e-4, torch.ones_like(q))
+    assert ei.value.status == mfc_lib.MFC_ERR_UNSUPPORTED
+    case.eta = [-1.0, 0.0]
+    with pytest.raises(mfc_lib.MfcError) as ei:
+        solver_for(mfc_lib, case)
+    assert ei.value.status == mfc_lib.MFC_ERR_ARG

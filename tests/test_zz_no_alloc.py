@@ -78,6 +78,18 @@ def test_noalloc_rejects_oversize_grid(mfc_lib, cuda_device):
     assert "too large" in mfc_lib.mfc_last_error(None)
 
 
+def test_noalloc_refuses_viscosity(mfc_lib, cuda_device):
+    """The allocation-free step has no scratch for the cell velocities of
+    the viscous stress: it refuses before touching the device."""
+    case, W = wl.taylor_green(dims=[8, 8, 8])
+    g, e, o = descriptors(mfc_lib, case)
+    e.eta[0] = case.eta[0]
+    q = torch.zeros(1, dtype=torch.float64, device=cuda_device)
+    with pytest.raises(mfc_lib.MfcError) as ei:
+        mfc_lib.mfc_rk3_step_noalloc(g, e, o, q.data_ptr(), 0.0, None, None)
+    assert ei.value.status == mfc_lib.MFC_ERR_UNSUPPORTED
+
+
 def test_noalloc_symbol_is_exported(mfc_lib):
     lib = ctypes.CDLL(mfc_lib.LIB_PATH)
     assert hasattr(lib, "mfc_rk3_step_noalloc")
