@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", default="shock_bubble_3d",
                     choices=["shock_bubble_3d", "random_interfaces_3d", "bubble_collapse_2d", "water_air_1d"])
     ap.add_argument("--n", type=int, default=0, help="cells per axis (0: the workload's own size)")
-    ap.add_argument("--precision", default="fp64_fast", choices=["fp64", "fp64_fast", "mixed"])
+    ap.add_argument("--precision", default="fp64_fast", choices=["fp64", "fp64_fast", "df64", "mixed"])
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed, adjoint, e2e and CPU legs")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -267,7 +267,7 @@ def make_workload_stub(args):
     return c
 
 
-PREC = {"fp64": 0, "mixed": 1, "fp64_fast": 2}
+PREC = {"fp64": 0, "mixed": 1, "fp64_fast": 2, "df64": 3}
 
 
 def time_vjp(S, q, dt: float, reps: int) -> float:
@@ -407,7 +407,7 @@ def run_ours(args, world, rank, local):
         line["field_max_rel_err_vs_fp64"] = field_errors(S.interior(qh), S.interior(qref), case.nf, case.ndim)
         line["after_steps"] = nsteps
         del qh
-        for name in ("fp64", "fp64_fast", "mixed"):
+        for name in ("fp64", "fp64_fast", "df64", "mixed"):
             if name == args.precision:
                 continue
             So = mfc.Solver.from_case(case, precision=PREC[name])

@@ -78,8 +78,20 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   differences (and their sum over directions) in float32; the
  *   cancelling part of the conservative-to-primitive conversion, the
  *   Runge-Kutta stage update and the CFL reduction in float64 (the CFL
- *   reduction with the MFC_FP64_FAST arithmetic). */
-typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2 } mfc_precision;
+ *   reduction with the MFC_FP64_FAST arithmetic).
+ * MFC_DF64: MFC_FP64_FAST with the WENO5 reconstruction (smoothness
+ *   indicators, weights, candidate values) in double-float arithmetic: pairs
+ *   of float32 values with a 48-bit significand, evaluated on the float32
+ *   pipes, which on GB300 run 64 times as many operations per clock as the
+ *   float64 pipe.  Everything else (conservative-to-primitive conversion,
+ *   HLLC, flux differences, stage update, CFL reduction) is the
+ *   MFC_FP64_FAST float64 arithmetic, so the two pipes work concurrently.
+ *   Agrees with MFC_FP64 to rounding (the same 1e-11 bar as MFC_FP64_FAST).
+ *   Primitive values must keep the smoothness indicators inside the
+ *   float32 range (differences across a stencil below ~1e18); an overflow
+ *   is reported as MFC_ERR_NONPHYSICAL.  The adjoint entry points of an MFC_DF64 context
+ *   run in the MFC_FP64_FAST arithmetic. */
+typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2, MFC_DF64 = 3 } mfc_precision;
 
 /* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2),
  * and fifth-order TENO (Sec. 4.2.2): the same three candidate stencils, each

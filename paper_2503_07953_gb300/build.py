@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libmfcgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["mfc_api.cu"] + [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast")]
+SOURCES = ["mfc_api.cu"] + [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast", "df")]
 # The exact-arithmetic kernels follow the defining formulas operation by
 # operation: no FMA contraction there.
 PER_SOURCE_FLAGS = {src: ["--fmad=false"] for src in SOURCES if src.endswith("_exact.cu")}
@@ -50,8 +50,8 @@ def _fingerprint() -> str:
 
 
 # The files the forward directional sweep kernels are compiled from.
-SWEEP_SOURCES = ["mfc_device.cuh", "mfc_fwd.cuh", "mfc_launch.h", "mfc_launch_impl.cuh"] + \
-    [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast")]
+SWEEP_SOURCES = ["mfc_df64.cuh", "mfc_device.cuh", "mfc_fwd.cuh", "mfc_launch.h", "mfc_launch_impl.cuh"] + \
+    [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast", "df")]
 
 
 def source_fingerprint() -> str:

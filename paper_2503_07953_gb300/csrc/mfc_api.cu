@@ -192,7 +192,8 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
         if (!(e->pi_inf[i] >= 0.0) || !std::isfinite(e->pi_inf[i])) return "pi_inf must be >= 0";
         if (!(e->eta[i] >= 0.0) || !std::isfinite(e->eta[i])) return "eta must be >= 0";
     }
-    if (o->precision != MFC_FP64 && o->precision != MFC_MIXED && o->precision != MFC_FP64_FAST)
+    if (o->precision != MFC_FP64 && o->precision != MFC_MIXED && o->precision != MFC_FP64_FAST &&
+        o->precision != MFC_DF64)
         return "unknown precision";
     if (o->weno < 0 || o->weno > 3) return "unknown WENO variant";
     if (o->weno == 3 && !(o->teno_ct > 0.0 && o->teno_ct < 1.0)) return "teno_ct must be in (0, 1)";
@@ -279,6 +280,37 @@ const mfc::LaunchFns* fast_fns_for(int nf) {
         case 2: return &mfc::launch_fns_fast_nf2();
         case 3: return &mfc::launch_fns_fast_nf3();
         default: return &mfc::launch_fns_fast_nf4();
+    }
+}
+
+// The MFC_DF64 tables: the fast table with the double-float sweeps.
+mfc::LaunchFns with_df_sweep(const mfc::LaunchFns& fast,
+                             cudaError_t (*sweep)(const mfc::Consts&, int, int, mfc::SweepArgs, cudaStream_t)) {
+    mfc::LaunchFns f = fast;
+    f.sweep = sweep;
+    return f;
+}
+
+const mfc::LaunchFns* df_fns_for(int nf) {
+    static const mfc::LaunchFns t1 = with_df_sweep(mfc::launch_fns_fast_nf1(), &mfc::sweep_df_nf1);
+    static const mfc::LaunchFns t2 = with_df_sweep(mfc::launch_fns_fast_nf2(), &mfc::sweep_df_nf2);
+    static const mfc::LaunchFns t3 = with_df_sweep(mfc::launch_fns_fast_nf3(), &mfc::sweep_df_nf3);
+    static const mfc::LaunchFns t4 = with_df_sweep(mfc::launch_fns_fast_nf4(), &mfc::sweep_df_nf4);
+    switch (nf) {
+        case 1: return &t1;
+        case 2: return &t2;
+        case 3: return &t3;
+        default: return &t4;
+    }
+}
+
+// Sweep table and arithmetic mode of a precision.
+void select_precision(int precision, int nf, const mfc::LaunchFns*& fns, int& mode) {
+    switch (precision) {
+        case MFC_FP64: fns = exact_fns_for(nf); mode = mfc::MODE_EXACT; break;
+        case MFC_MIXED: fns = fast_fns_for(nf); mode = mfc::MODE_MIXED; break;
+        case MFC_DF64: fns = df_fns_for(nf); mode = mfc::MODE_DF; break;
+        default: fns = fast_fns_for(nf); mode = mfc::MODE_FAST; break;
     }
 }
 
@@ -581,13 +613,7 @@ mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* op
     ctx->opts = *opts;
     make_consts(grid, eos, opts, ctx->C, ctx->total);
     ctx->exact = exact_fns_for(eos->nfluids);
-    if (opts->precision == MFC_FP64) {
-        ctx->fns = ctx->exact;
-        ctx->mode = mfc::MODE_EXACT;
-    } else {
-        ctx->fns = fast_fns_for(eos->nfluids);
-        ctx->mode = opts->precision == MFC_MIXED ? mfc::MODE_MIXED : mfc::MODE_FAST;
-    }
+    select_precision(opts->precision, eos->nfluids, ctx->fns, ctx->mode);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
         g_init_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
@@ -835,13 +861,7 @@ extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* 
     ctx.opts = *opts;
     ctx.device = dev;
     ctx.exact = exact_fns_for(eos->nfluids);
-    if (opts->precision == MFC_FP64) {
-        ctx.fns = ctx.exact;
-        ctx.mode = mfc::MODE_EXACT;
-    } else {
-        ctx.fns = fast_fns_for(eos->nfluids);
-        ctx.mode = opts->precision == MFC_MIXED ? mfc::MODE_MIXED : mfc::MODE_FAST;
-    }
+    select_precision(opts->precision, eos->nfluids, ctx.fns, ctx.mode);
     ctx.scal = reinterpret_cast<DevScalars*>(base);
     ctx.q1 = base + kNoallocScalarDoubles;
     ctx.q2 = ctx.q1 + ctx.total;

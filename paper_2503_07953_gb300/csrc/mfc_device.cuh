@@ -11,20 +11,29 @@
 //               repeated divisions, and FMA contraction;
 //   MODE_MIXED  the MODE_FAST formulas in float32 for reconstruction, the
 //               Riemann solve and the per-direction flux difference;
-//               conservative-to-primitive conversion stays float64.
+//               conservative-to-primitive conversion stays float64;
+//   MODE_DF     MODE_FAST with the WENO5 weights and candidate corrections
+//               in double-float arithmetic (mfc_df64.cuh) on the float32
+//               pipes; the Riemann solve and everything else stay in
+//               MODE_FAST's float64, so both pipes work at once.
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mfc_df64.cuh"
+
 namespace mfc {
 
 constexpr int MAXF = 4;
 
-enum { MODE_EXACT = 0, MODE_MIXED = 1, MODE_FAST = 2 };
+enum { MODE_EXACT = 0, MODE_MIXED = 1, MODE_FAST = 2, MODE_DF = 3 };
 
-template <int MODE> struct ModeT { using R = double; };
-template <> struct ModeT<MODE_MIXED> { using R = float; };
+// R: precision of the Riemann solve and flux difference; RW: precision of
+// the primitive states the reconstruction reads.
+template <int MODE> struct ModeT { using R = double; using RW = double; };
+template <> struct ModeT<MODE_MIXED> { using R = float; using RW = float; };
+template <> struct ModeT<MODE_DF> { using R = double; using RW = double; };
 
 // Everything a kernel needs to know about the grid, layout and fluids.
 // Passed by value as a kernel parameter.
@@ -436,6 +445,164 @@ __device__ __forceinline__ void teno_weights(const R* b, R e, R ct, const R* dR,
         oms[s][1] = a1 * inv;
         oms[s][2] = a2 * inv;
     }
+}
+
+// MODE_DF: WENO5 of one cell in double-float arithmetic, the same
+// smoothness indicators, candidate polynomials and weight functions as the
+// float64 modes, written on the consecutive differences D_j = f_{j+1} - f_j
+// of the stencil (taken in float64, then carried as double-float): the
+// indicators depend only on differences, and each candidate value is
+// f2 + (a combination of differences) / 6, because the candidate
+// coefficients sum to one.  So constant data reconstruct exactly, and the
+// double-float rounding applies to the corrections, not to the values.
+// The weights depend only on ratios of t_r = eps + beta_r.  The t_r are
+// scaled by the power of two that brings the largest into [1, 2) (exact)
+// and floored at 2^-120; JS and mapped use u_r = t_min / t_r in (0, 1]
+// (alpha_r = d_r u_r^2), Z and TENO use A_r = 1 + tau / t_r divided by
+// max A, so no weight or normaliser leaves the normal float32 range where
+// it matters.  The floor only moves weight between stencils whose
+// indicators are below 2^-120 of the largest, and the candidates of two
+// such stencils differ by at most (sqrt(beta_r) + sqrt(beta_s)) / 3 <
+// 2^-60 sqrt(beta_max).  When every t_r is below 2^-120 (data flat to
+// ~1e-18) the ideal weights are used, which is what alpha_r = d_r / eps^2
+// gives.  bad is set when an indicator overflows the float32 range
+// (differences above ~1e18).  One call per field: not inlined, so a single
+// copy of its code serves all fields from the instruction cache; the
+// result is returned by value so that it stays in registers.
+struct WenoEdges {
+    double vl, vr;
+    int bad;
+};
+
+static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, double f2, double f3, double f4, int variant,
+                                                       double eps, double ct) {
+    constexpr df64 c13(13.0 / 12.0), sixth(1.0 / 6.0), one(1.0);
+    const df64 D01(f1 - f0), D12(f2 - f1), D23(f3 - f2), D34(f4 - f3);
+    // smoothness indicators: beta_r = 13/12 a_r^2 + 1/4 g_r^2
+    const df64 a0 = D12 - D01, g0 = df_mulf(D12, 3.0f) - D01;
+    const df64 a1 = D23 - D12, g1 = D12 + D23;
+    const df64 a2 = D34 - D23, g2 = D34 - df_mulf(D23, 3.0f);
+    const df64 e(eps);
+    df64 t[3];
+    t[0] = e + (c13 * (a0 * a0) + df_scale(g0 * g0, 0.25f));
+    t[1] = e + (c13 * (a1 * a1) + df_scale(g1 * g1, 0.25f));
+    t[2] = e + (c13 * (a2 * a2) + df_scale(g2 * g2, 0.25f));
+    // 6 (candidate - f2) at the right (P) and left (Q) edges
+    const df64 P[3] = {df_mulf(D12, 5.0f) - df_scale(D01, 2.0f), D12 + df_scale(D23, 2.0f),
+                       df_scale(D23, 4.0f) - D34};
+    const df64 Q[3] = {D01 - df_scale(D12, 4.0f), -(df_scale(D12, 2.0f) + D23),
+                       df_scale(D34, 2.0f) - df_mulf(D23, 5.0f)};
+    const double dR[3] = {0.1, 0.6, 0.3}, dL[3] = {0.3, 0.6, 0.1};
+    df64 omR[3], omL[3];
+    const float th = fmaxf(fmaxf(t[0].hi, t[1].hi), t[2].hi);
+    WenoEdges out;
+    // an indicator that overflowed is inf or NaN, and so is the sum
+    out.bad = !((t[0].hi + t[1].hi) + t[2].hi <= 0x1.fffffep127f);
+    if (!(th >= 0x1p-120f)) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            omR[r] = df64(dR[r]);
+            omL[r] = df64(dL[r]);
+        }
+    } else {
+        int k = ((__float_as_int(th) >> 23) & 0xff) - 127;
+        k = k > 126 ? 126 : k;
+        const float s = __int_as_float((127 - k) << 23);
+        df64 ts[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ts[r] = df_scale(t[r], s);
+            if (ts[r].hi < 0x1p-120f) ts[r] = df64(0x1p-120f, 0.0f);
+        }
+        if (variant == WENO_Z || variant == WENO_TENO) {
+            // A_r = 1 + tau / t_r with tau = |beta_0 - beta_2|, as B_r = A_r / max A
+            const df64 tau = df_abs(df_scale(t[0], s) - df_scale(t[2], s));
+            df64 B[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) B[r] = one + df_div(tau, ts[r]);
+            df64 Am = (B[1] > B[0]) ? B[1] : B[0];
+            Am = (B[2] > Am) ? B[2] : Am;
+            const df64 iAm = df_div(one, Am);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) B[r] = B[r] * iAm;
+            if (variant == WENO_Z) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const double* d = side ? dL : dR;
+                    df64* om = side ? omL : omR;
+                    const df64 x0 = df64(d[0]) * B[0], x1 = df64(d[1]) * B[1], x2 = df64(d[2]) * B[2];
+                    const df64 inv = df_div(one, (x0 + x1) + x2);
+                    om[0] = x0 * inv;
+                    om[1] = x1 * inv;
+                    om[2] = x2 * inv;
+                }
+            } else {
+                // TENO: gamma_r = d_r B_r^6; stencil r off when gamma_r < C_T sum
+                // gamma, the others at d_r renormalised
+                df64 x6[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const df64 x2 = B[r] * B[r];
+                    x6[r] = x2 * (x2 * x2);
+                }
+                const df64 cT(ct);
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const double* d = side ? dL : dR;
+                    df64* om = side ? omL : omR;
+                    const df64 y0 = df64(d[0]) * x6[0], y1 = df64(d[1]) * x6[1], y2 = df64(d[2]) * x6[2];
+                    const df64 lim = cT * ((y0 + y1) + y2);
+                    const df64 b0 = (y0 < lim) ? df64(0.0) : df64(d[0]);
+                    const df64 b1 = (y1 < lim) ? df64(0.0) : df64(d[1]);
+                    const df64 b2 = (y2 < lim) ? df64(0.0) : df64(d[2]);
+                    const df64 inv = df_div(one, (b0 + b1) + b2);
+                    om[0] = b0 * inv;
+                    om[1] = b1 * inv;
+                    om[2] = b2 * inv;
+                }
+            }
+        } else {
+            // JS and mapped: alpha_r proportional to d_r (t_min / t_r)^2
+            const float tmh = fminf(fminf(ts[0].hi, ts[1].hi), ts[2].hi);
+            const df64 tmin = (ts[0].hi == tmh) ? ts[0] : ((ts[1].hi == tmh) ? ts[1] : ts[2]);
+            df64 u2[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const df64 u = df_div(tmin, ts[r]);
+                u2[r] = u * u;
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const double* d = side ? dL : dR;
+                df64* om = side ? omL : omR;
+                df64 w[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) w[r] = df64(d[r]) * u2[r];
+                df64 inv = df_div(one, (w[0] + w[1]) + w[2]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) w[r] = w[r] * inv;
+                if (variant == WENO_M) {
+                    // g_r(w) = w (d + d^2 - 3 d w + w^2) / (d^2 + w (1 - 2 d)), renormalised
+                    df64 N[3], D[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        N[r] = w[r] * (df64(d[r] * (1.0 + d[r])) + w[r] * (w[r] - df64(3.0 * d[r])));
+                        D[r] = df64(d[r] * d[r]) + w[r] * df64(1.0 - 2.0 * d[r]);
+                    }
+                    const df64 gm0 = N[0] * (D[1] * D[2]), gm1 = N[1] * (D[0] * D[2]), gm2 = N[2] * (D[0] * D[1]);
+                    inv = df_div(one, (gm0 + gm1) + gm2);
+                    w[0] = gm0 * inv;
+                    w[1] = gm1 * inv;
+                    w[2] = gm2 * inv;
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) om[r] = w[r];
+            }
+        }
+    }
+    out.vr = f2 + double(((omR[0] * P[0] + omR[1] * P[1]) + omR[2] * P[2]) * sixth);
+    out.vl = f2 + double(((omL[0] * Q[0] + omL[1] * Q[1]) + omL[2] * Q[2]) * sixth);
+    return out;
 }
 
 template <int MODE, class R>

@@ -1,0 +1,123 @@
+// Double-float arithmetic: a real number carried as the unevaluated sum of
+// two float32 values, hi + lo with |lo| <= ulp(hi)/2 (a 48-bit significand
+// with float32's exponent range).  Every operation runs on the float32
+// pipes, which on GB300 execute 64 times more operations per clock than the
+// float64 pipe.
+//
+// The building blocks are the error-free transformations of Dekker (1971)
+// and Knuth (TAOCP vol. 2): the rounding error of a float32 sum is
+// recovered exactly by TwoSum, that of a product by one fused multiply-add.
+// Addition is the "sloppy" double-float sum (error bounded by a small
+// multiple of 2^-48 (|a| + |b|), as for a rounded float64 sum of inputs
+// that carry their own rounding); multiplication, division and square root
+// are accurate to a few units of 2^-48 relative.  All steps use the
+// explicitly rounded intrinsics so the compiler neither contracts nor
+// reassociates them, whatever the translation unit's FMA setting.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mfc {
+
+struct df64 {
+    float hi, lo;
+    df64() = default;
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    // nearest double-float to a float64 value: hi is x rounded to float32,
+    // lo the rounded remainder (x - hi is exact in float64)
+    __host__ __device__ explicit constexpr df64(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// s + e as a normalised pair when |s| >= |e| (Dekker's Fast2Sum)
+__device__ __forceinline__ df64 df_fast2sum(float s, float e) {
+    const float h = __fadd_rn(s, e);
+    return df64(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    // TwoSum of the leading parts, then the trailing parts folded into the error
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return df_fast2sum(s, e);
+}
+
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // exact rounding error of a.hi b.hi
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast2sum(p, e);
+}
+
+// a times a float32 value b
+__device__ __forceinline__ df64 df_mulf(df64 a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df_fast2sum(p, e);
+}
+
+// a times a power of two (exact barring overflow and underflow)
+__device__ __forceinline__ df64 df_scale(df64 a, float two_pow) {
+    return df64(__fmul_rn(a.hi, two_pow), __fmul_rn(a.lo, two_pow));
+}
+
+// float32 reciprocal: the hardware approximation (1 ulp) refined by one
+// Newton step, r <- r + r (1 - b r)
+__device__ __forceinline__ float rcp_f32(float b) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(b));
+    const float e = __fmaf_rn(-b, r, 1.0f);
+    return __fmaf_rn(r, e, r);
+}
+
+// a / b: a float32 quotient q1 = a.hi / b.hi, the remainder a - q1 b in
+// double-float (its leading part is exact by Sterbenz's lemma), and the
+// correction q2 = remainder / b.hi.
+__device__ __forceinline__ df64 df_div(df64 a, df64 b) {
+    const float r = rcp_f32(b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    const float p = __fmul_rn(q1, b.hi);
+    const float pe = __fmaf_rn(q1, b.hi, -p);
+    float rem = __fsub_rn(a.hi, p);
+    rem = __fsub_rn(rem, pe);
+    rem = __fadd_rn(rem, a.lo);
+    rem = __fmaf_rn(-q1, b.lo, rem);
+    return df_fast2sum(q1, __fmul_rn(rem, r));
+}
+
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return df_div(a, b); }
+
+// sqrt(a): y = a.hi x with x a refined 1/sqrt(a.hi), then one Newton
+// correction y + (a - y^2) / (2 y) with the residual in double-float.
+__device__ __forceinline__ df64 df_sqrt(df64 a) {
+    if (!(a.hi > 0.0f)) return df64(sqrtf(a.hi), 0.0f);  // 0 -> 0, negative or NaN -> NaN
+    float x;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(x) : "f"(a.hi));
+    // x <- x (3 - a x^2) / 2
+    x = __fmul_rn(x, __fmaf_rn(__fmul_rn(-0.5f, a.hi), __fmul_rn(x, x), 1.5f));
+    const float y = __fmul_rn(a.hi, x);
+    const float p = __fmul_rn(y, y);
+    const float pe = __fmaf_rn(y, y, -p);
+    float rem = __fsub_rn(a.hi, p);
+    rem = __fsub_rn(rem, pe);
+    rem = __fadd_rn(rem, a.lo);
+    return df_fast2sum(y, __fmul_rn(rem, __fmul_rn(0.5f, x)));
+}
+
+__device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
+
+// Comparisons of normalised pairs: by the leading part, then the trailing part.
+__device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
+__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
+
+}  // namespace mfc

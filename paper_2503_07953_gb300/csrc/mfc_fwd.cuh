@@ -23,6 +23,7 @@ template <int NF, int ND, int DIR, int MODE>
 __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) {
     using L = Lay<NF, ND>;
     using R = typename ModeT<MODE>::R;
+    using RW = typename ModeT<MODE>::RW;
     constexpr int NQ = L::NQ;
     constexpr int TA = (DIR == 0) ? 1 : 0;
     constexpr int TB = (DIR == 2) ? 1 : 2;
@@ -46,8 +47,8 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
     const double dx = C.dx[DIR];
     bool bad = false;
 
-    R W[5][NQ];
-    auto load_prim = [&](int64_t c, R* out) {
+    RW W[5][NQ];
+    auto load_prim = [&](int64_t c, RW* out) {
         bool flip = false;
         const int64_t cc = bc_source(c, n, bclo, bchi, flip);
         const double* p = A.q + base + cc * S;
@@ -55,7 +56,7 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
 #pragma unroll
         for (int f = 0; f < NQ; ++f) qc[f] = __ldg(p + f * C.fstride);
         if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
-        prim_for_recon<NF, ND, MODE, R>(qc, out, C, bad);
+        prim_for_recon<NF, ND, MODE, RW>(qc, out, C, bad);
     };
 
 #pragma unroll
@@ -93,15 +94,23 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
         load_prim(m + 2, W[4]);
         R WRm[NQ], WLm[NQ];
 #pragma unroll
-        for (int k = 0; k < NQ; ++k)
-            weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
+        for (int k = 0; k < NQ; ++k) {
+            if constexpr (MODE == MODE_DF) {
+                const WenoEdges e = weno5_cell_df(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, C.eps,
+                                                  C.teno_ct);
+                WRm[k] = e.vl;
+                WLm[k] = e.vr;
+                bad |= e.bad != 0;
+            } else
+                weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
+        }
         if (m >= s0) {
             // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)
             if (!physical_state<NF, ND, R, MODE>(WLprev, C) || !physical_state<NF, ND, R, MODE>(WRm, C)) {
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    WLprev[k] = W[1][k];
-                    WRm[k] = W[2][k];
+                    WLprev[k] = R(W[1][k]);
+                    WRm[k] = R(W[2][k]);
                 }
             }
             R F[NQ], uf;
@@ -113,12 +122,12 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
                 // alpha rows: alpha div u, or (alpha + K) div u (Kapila)
                 R Kc = R(0);
                 if constexpr (NF == 2) {
-                    if (C.model == 1) Kc = kapila_K<MODE, R>(W[1][L::E], W[1][L::A], C);
+                    if (C.model == 1) Kc = kapila_K<MODE, R>(R(W[1][L::E]), R(W[1][L::A]), C);
                 }
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     R t;
-                    const R ac = (k >= L::A && C.model == 1) ? W[1][k] + Kc : W[1][k];
+                    const R ac = (k >= L::A && C.model == 1) ? R(W[1][k]) + Kc : R(W[1][k]);
                     if constexpr (MODE == MODE_EXACT) {
                         t = (Fprev[k] - F[k]) / dx;
                         if (k >= L::A) t = t + ac * du / dx;

@@ -73,6 +73,14 @@ const LaunchFns& launch_fns_fast_nf2();
 const LaunchFns& launch_fns_fast_nf3();
 const LaunchFns& launch_fns_fast_nf4();
 
+// MODE_DF directional sweeps for N_f = 1 .. 4 (mfc_nf<NF>_df.cu).  The
+// double-float mode's other entries (adjoint, CFL, viscous) are those of
+// the fast tables, in MODE_FAST arithmetic.
+cudaError_t sweep_df_nf1(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+cudaError_t sweep_df_nf2(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+cudaError_t sweep_df_nf3(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+cudaError_t sweep_df_nf4(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+
 // Cells per thread along a sweep of `n` cells with `nlines` lines.
 int sweep_segment(int64_t n, int64_t nlines);
 

@@ -108,6 +108,32 @@ cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream
     return cudaGetLastError();
 }
 
+// MODE_DF sweeps: the per-thread march in every direction and on every
+// grid (its float64 share is what bounds it, and the march keeps that
+// share smallest).
+template <int NF, int ND>
+cudaError_t sweep_df_nd(const Consts& C, int dir, SweepArgs A, cudaStream_t s) {
+    const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];
+    A.seg = sweep_segment(C.n[dir], nlines);
+    A.nseg = (int)((C.n[dir] + A.seg - 1) / A.seg);
+    const int64_t threads = nlines * A.nseg;
+    if (threads == 0) return cudaSuccess;
+    const unsigned grid = grid_for(threads, kSweepBlock);
+    if (dir == 0) launch_sweep<NF, ND, 0, MODE_DF>(grid, C, A, s);
+    if constexpr (ND >= 2) if (dir == 1) launch_sweep<NF, ND, 1, MODE_DF>(grid, C, A, s);
+    if constexpr (ND >= 3) if (dir == 2) launch_sweep<NF, ND, 2, MODE_DF>(grid, C, A, s);
+    return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t sweep_df(const Consts& C, int dir, int, SweepArgs A, cudaStream_t s) {
+    switch (C.nd) {
+        case 1: return sweep_df_nd<NF, 1>(C, dir, A, s);
+        case 2: return sweep_df_nd<NF, 2>(C, dir, A, s);
+        default: return sweep_df_nd<NF, 3>(C, dir, A, s);
+    }
+}
+
 template <int NF, int ND, bool EXACT>
 cudaError_t sweep_vjp_nd(const Consts& C, int dir, int mode, VjpArgs A, cudaStream_t s) {
     const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];

@@ -1,0 +1,8 @@
+// Directional sweeps for 3 fluid(s) in MODE_DF (double-float WENO5).
+#include "mfc_launch_impl.cuh"
+
+namespace mfc {
+cudaError_t sweep_df_nf3(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s) {
+    return sweep_df<3>(C, dir, mode, A, s);
+}
+}  // namespace mfc

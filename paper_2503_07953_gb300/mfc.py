@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmfcgb.so")
 
 MFC_OK, MFC_ERR_ARG, MFC_ERR_ALLOC, MFC_ERR_CUDA, MFC_ERR_NONPHYSICAL, MFC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE = 0, 1, 2
-MFC_FP64, MFC_MIXED, MFC_FP64_FAST = 0, 1, 2
+MFC_FP64, MFC_MIXED, MFC_FP64_FAST, MFC_DF64 = 0, 1, 2, 3
 MFC_WENO_JS, MFC_WENO_M, MFC_WENO_Z, MFC_WENO_TENO = 0, 1, 2, 3
 MFC_MODEL_K0, MFC_MODEL_KAPILA = 0, 1
 MFC_RIEMANN_HLLC, MFC_RIEMANN_HLL = 0, 1
