@@ -465,8 +465,8 @@ __device__ __forceinline__ void teno_weights(const R* b, R e, R ct, const R* dR,
 // such stencils differ by at most (sqrt(beta_r) + sqrt(beta_s)) / 3 <
 // 2^-60 sqrt(beta_max).  When every t_r is below 2^-120 (data flat to
 // ~1e-18) the ideal weights are used, which is what alpha_r = d_r / eps^2
-// gives.  bad is set when an indicator overflows the float32 range
-// (differences above ~1e18).  One call per field: not inlined, so a single
+// gives.  e and cT are eps and C_T as double-float.  bad is set when an
+// indicator overflows the float32 range (differences above ~1e18).  One call per field: not inlined, so a single
 // copy of its code serves all fields from the instruction cache; the
 // result is returned by value so that it stays in registers.
 struct WenoEdges {
@@ -474,15 +474,15 @@ struct WenoEdges {
     int bad;
 };
 
-static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, double f2, double f3, double f4, int variant,
-                                                       double eps, double ct) {
+static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, double f2, double f3, double f4,
+                                                       int variant, df64 e, df64 cT) {
     constexpr df64 c13(13.0 / 12.0), sixth(1.0 / 6.0), one(1.0);
-    const df64 D01(f1 - f0), D12(f2 - f1), D23(f3 - f2), D34(f4 - f3);
+    const df64 D01 = df_from_f64_bits(f1 - f0), D12 = df_from_f64_bits(f2 - f1);
+    const df64 D23 = df_from_f64_bits(f3 - f2), D34 = df_from_f64_bits(f4 - f3);
     // smoothness indicators: beta_r = 13/12 a_r^2 + 1/4 g_r^2
     const df64 a0 = D12 - D01, g0 = df_mulf(D12, 3.0f) - D01;
     const df64 a1 = D23 - D12, g1 = D12 + D23;
     const df64 a2 = D34 - D23, g2 = D34 - df_mulf(D23, 3.0f);
-    const df64 e(eps);
     df64 t[3];
     t[0] = e + (c13 * (a0 * a0) + df_scale(g0 * g0, 0.25f));
     t[1] = e + (c13 * (a1 * a1) + df_scale(g1 * g1, 0.25f));
@@ -545,7 +545,6 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
                     const df64 x2 = B[r] * B[r];
                     x6[r] = x2 * (x2 * x2);
                 }
-                const df64 cT(ct);
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     const double* d = side ? dL : dR;
@@ -600,8 +599,10 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
             }
         }
     }
-    out.vr = f2 + double(((omR[0] * P[0] + omR[1] * P[1]) + omR[2] * P[2]) * sixth);
-    out.vl = f2 + double(((omL[0] * Q[0] + omL[1] * Q[1]) + omL[2] * Q[2]) * sixth);
+    const df64 cr = ((omR[0] * P[0] + omR[1] * P[1]) + omR[2] * P[2]) * sixth;
+    const df64 cl = ((omL[0] * Q[0] + omL[1] * Q[1]) + omL[2] * Q[2]) * sixth;
+    out.vr = f2 + (f64_from_f32_bits(cr.hi) + f64_from_f32_bits(cr.lo));
+    out.vl = f2 + (f64_from_f32_bits(cl.hi) + f64_from_f32_bits(cl.lo));
     return out;
 }
 

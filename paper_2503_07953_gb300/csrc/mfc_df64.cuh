@@ -114,6 +114,41 @@ __device__ __forceinline__ df64 df_sqrt(df64 a) {
 
 __device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
 
+// Conversions between float64 and double-float by integer operations on
+// the bit patterns.  On GB300 the float32 <-> float64 conversion
+// instructions run on the float64 pipe, the scarcest unit here; these run
+// on the integer pipe (and one int -> float32 conversion).
+
+// Nearest double-float of x: the leading part is x rounded to 24
+// significant bits (a carry out of the mantissa moves into the exponent),
+// the trailing part the signed remainder, at most half an ulp of the
+// leading part, rounded to float32.  Exact to 2^-48 relative for
+// 2^-74 <= |x| < 2^128; smaller magnitudes keep only their leading part
+// (zero below 2^-126), larger ones become infinite, NaN stays NaN.
+__device__ __forceinline__ df64 df_from_f64_bits(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned s = hi & 0x80000000u;
+    const unsigned e = (hi >> 20) & 0x7ffu;  // biased float64 exponent
+    const unsigned up = (lo >> 28) & 1u;     // the first dropped bit rounds the leading part
+    unsigned h = (((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + up;
+    const int rem = (int)(lo & 0x1fffffffu) - (int)(up << 29);  // remainder in units of 2^(e - 1075)
+    float t = (float)rem * __uint_as_float((e - 948u) << 23);
+    if (e < 949u || e > 1150u) t = 0.0f;
+    if (e < 897u) h = 0u;
+    if (e > 1150u) h = (e == 2047u && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    return df64(__uint_as_float(s | h), __uint_as_float(__float_as_uint(t) ^ s));
+}
+
+// A float32 value as float64 (exact for normal numbers; subnormals become
+// zero, infinities and NaN keep their class).
+__device__ __forceinline__ double f64_from_f32_bits(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = (e == 0u) ? 0u : (b & 0x7fffffu);
+    const unsigned de = (e == 0u) ? 0u : ((e == 0xffu) ? 0x7ffu : e + 896u);
+    return __hiloint2double((int)((b & 0x80000000u) | (de << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // Comparisons of normalised pairs: by the leading part, then the trailing part.
 __device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }

@@ -45,6 +45,7 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
     const R ct = sizeof(R) == 8 ? R(C.teno_ct) : R(C.teno_ctf);
     const R inv_dx = sizeof(R) == 8 ? R(C.inv_dx[DIR]) : R(C.inv_dxf[DIR]);
     const double dx = C.dx[DIR];
+    const df64 eps_df(C.eps), ct_df(C.teno_ct);
     bool bad = false;
 
     RW W[5][NQ];
@@ -96,8 +97,8 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             if constexpr (MODE == MODE_DF) {
-                const WenoEdges e = weno5_cell_df(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, C.eps,
-                                                  C.teno_ct);
+                const WenoEdges e = weno5_cell_df(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps_df,
+                                                  ct_df);
                 WRm[k] = e.vl;
                 WLm[k] = e.vr;
                 bad |= e.bad != 0;
