@@ -38,7 +38,7 @@ from . import adjoint as adj
 from . import checkpoint, flops, mfc
 from . import workloads as wl
 
-PREC = {"fp64": mfc.MFC_FP64, "fp64_fast": mfc.MFC_FP64_FAST, "mixed": mfc.MFC_MIXED}
+PREC = {"fp64": mfc.MFC_FP64, "fp64_fast": mfc.MFC_FP64_FAST, "df64": mfc.MFC_DF64, "mixed": mfc.MFC_MIXED}
 
 
 def _emit(rec: dict) -> None:
@@ -219,7 +219,7 @@ def main(argv=None) -> None:
     sub = ap.add_subparsers(dest="study", required=True)
     p = sub.add_parser("sizes")
     p.add_argument("--sizes", type=int, nargs="+", default=[128, 256, 384, 512, 640])
-    p.add_argument("--precisions", nargs="+", default=["fp64_fast", "mixed"], choices=sorted(PREC))
+    p.add_argument("--precisions", nargs="+", default=["fp64_fast", "df64", "mixed"], choices=sorted(PREC))
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--no-vjp", dest="vjp", action="store_false")
