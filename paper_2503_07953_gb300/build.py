@@ -50,7 +50,8 @@ def _fingerprint() -> str:
 
 
 # The files the forward directional sweep kernels are compiled from.
-SWEEP_SOURCES = ["mfc_df64.cuh", "mfc_device.cuh", "mfc_fwd.cuh", "mfc_launch.h", "mfc_launch_impl.cuh"] + \
+SWEEP_SOURCES = ["mfc_df64.cuh", "mfc_device.cuh", "mfc_fwd.cuh", "mfc_split.cuh", "mfc_launch.h",
+                 "mfc_launch_impl.cuh"] + \
     [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast", "df")]
 
 

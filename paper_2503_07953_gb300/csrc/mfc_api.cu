@@ -60,6 +60,15 @@ struct mfc_ctx {
     cudaEvent_t ev_in[2] = {nullptr, nullptr};
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_out[2] = {nullptr, nullptr};
+    // split double-float sweeps (MFC_DF64; created at init): the stream that
+    // runs the reconstructions, its fork event, a ring of edge-value buffers
+    // with an event per slot for "filled" and "read", lines per chunk per axis
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_filled[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_read[3] = {nullptr, nullptr, nullptr};
+    double* ebuf[3] = {nullptr, nullptr, nullptr};
+    int64_t chunk_lines[3] = {0, 0, 0};
     DevScalars* scal = nullptr;
     std::string err;
 };
@@ -285,17 +294,20 @@ const mfc::LaunchFns* fast_fns_for(int nf) {
 
 // The MFC_DF64 tables: the fast table with the double-float sweeps.
 mfc::LaunchFns with_df_sweep(const mfc::LaunchFns& fast,
-                             cudaError_t (*sweep)(const mfc::Consts&, int, int, mfc::SweepArgs, cudaStream_t)) {
+                             cudaError_t (*sweep)(const mfc::Consts&, int, int, mfc::SweepArgs, cudaStream_t),
+                             cudaError_t (*split)(const mfc::Consts&, int, int, mfc::SweepArgs, mfc::SplitChunk,
+                                                  cudaStream_t)) {
     mfc::LaunchFns f = fast;
     f.sweep = sweep;
+    f.split_sweep = split;
     return f;
 }
 
 const mfc::LaunchFns* df_fns_for(int nf) {
-    static const mfc::LaunchFns t1 = with_df_sweep(mfc::launch_fns_fast_nf1(), &mfc::sweep_df_nf1);
-    static const mfc::LaunchFns t2 = with_df_sweep(mfc::launch_fns_fast_nf2(), &mfc::sweep_df_nf2);
-    static const mfc::LaunchFns t3 = with_df_sweep(mfc::launch_fns_fast_nf3(), &mfc::sweep_df_nf3);
-    static const mfc::LaunchFns t4 = with_df_sweep(mfc::launch_fns_fast_nf4(), &mfc::sweep_df_nf4);
+    static const mfc::LaunchFns t1 = with_df_sweep(mfc::launch_fns_fast_nf1(), &mfc::sweep_df_nf1, &mfc::split_df_nf1);
+    static const mfc::LaunchFns t2 = with_df_sweep(mfc::launch_fns_fast_nf2(), &mfc::sweep_df_nf2, &mfc::split_df_nf2);
+    static const mfc::LaunchFns t3 = with_df_sweep(mfc::launch_fns_fast_nf3(), &mfc::sweep_df_nf3, &mfc::split_df_nf3);
+    static const mfc::LaunchFns t4 = with_df_sweep(mfc::launch_fns_fast_nf4(), &mfc::sweep_df_nf4, &mfc::split_df_nf4);
     switch (nf) {
         case 1: return &t1;
         case 2: return &t2;
@@ -327,6 +339,109 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
     return MFC_OK;
 }
 
+constexpr int kSplitSlots = 3;
+
+// Lines per chunk of a split sweep along `dir`: enough chunks that the
+// reconstruction of one runs beside the Riemann solve of another, each
+// chunk about two 128-thread blocks per SM of either kernel.
+int64_t split_chunk_lines(const mfc::Consts& C, int dir) {
+    const int64_t n = C.n[dir];
+    const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / n;
+    const int64_t seg = mfc::sweep_segment(n, nlines);
+    const int64_t nseg = (n + seg - 1) / seg;
+    int64_t chunks = nlines * nseg / (152LL * 128 * 2);
+    if (chunks < 1) chunks = 1;
+    if (chunks > 16) chunks = 16;
+    return (nlines + chunks - 1) / chunks;
+}
+
+// Stream, events and edge-value ring of the split MFC_DF64 sweeps.
+mfc_status create_split(mfc_ctx* ctx) {
+    const mfc::Consts& C = ctx->C;
+    size_t doubles = 0;
+    for (int d = 0; d < C.nd; ++d) {
+        ctx->chunk_lines[d] = split_chunk_lines(C, d);
+        const size_t need = (size_t)2 * C.nq * (size_t)(C.n[d] + 2) * (size_t)ctx->chunk_lines[d];
+        if (need > doubles) doubles = need;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < kSplitSlots && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ctx->ev_filled[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_read[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->ebuf[i], doubles * sizeof(double));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? MFC_ERR_ALLOC : MFC_ERR_CUDA;
+    }
+    return MFC_OK;
+}
+
+void destroy_split(mfc_ctx* ctx) {
+    for (int i = 0; i < kSplitSlots; ++i) {
+        if (ctx->ebuf[i]) cudaFree(ctx->ebuf[i]);
+        if (ctx->ev_filled[i]) cudaEventDestroy(ctx->ev_filled[i]);
+        if (ctx->ev_read[i]) cudaEventDestroy(ctx->ev_read[i]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+}
+
+// The directional sweeps of one evaluation of L in MFC_DF64, split: for each
+// direction and chunk of lines, the reconstruction on ctx->side into a slot
+// of the ring, then the Riemann solve and update from it on s.  A slot is
+// refilled only after the Riemann kernel that read it (3 chunks earlier)
+// is done; the reconstructions start after everything queued on s before
+// this call.  Same SweepArgs as the fused sweeps of eval_L.
+mfc_status eval_L_split(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, const double* qn,
+                        double* qout, double a, double b, cudaStream_t s) {
+    const mfc::Consts& C = ctx->C;
+    cudaError_t e = cudaEventRecord(ctx->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "split sweep: fork");
+    if (C.viscous) {
+        e = ctx->fns->viscous(C, ctx->mode, qin, ctx->vel, rhs, nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "viscous kernels");
+    }
+    int64_t j = 0;
+    for (int d = 0; d < C.nd; ++d) {
+        mfc::SweepArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.q = qin;
+        A.rhs = rhs;
+        A.acc_in = (d == 0 && !C.viscous) ? 0 : 1;
+        A.out_kind = d == C.nd - 1 ? out_kind : 0;
+        A.qn = qn;
+        A.qout = qout;
+        A.dt = &ctx->scal->dt;
+        A.rk_a = a;
+        A.rk_b = b;
+        A.flag = &ctx->scal->flag;
+        const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[d];
+        const int64_t per = ctx->chunk_lines[d];
+        for (int64_t l0 = 0; l0 < nlines; l0 += per, ++j) {
+            const int slot = (int)(j % kSplitSlots);
+            mfc::SplitChunk K;
+            K.line0 = l0;
+            K.nl = (nlines - l0 < per) ? nlines - l0 : per;
+            K.E = ctx->ebuf[slot];
+            if (j >= kSplitSlots && (e = cudaStreamWaitEvent(ctx->side, ctx->ev_read[slot], 0)) != cudaSuccess)
+                return cuda_fail(ctx, e, "split sweep: slot wait");
+            if ((e = ctx->fns->split_sweep(C, d, 0, A, K, ctx->side)) != cudaSuccess)
+                return cuda_fail(ctx, e, "reconstruction kernel");
+            if ((e = cudaEventRecord(ctx->ev_filled[slot], ctx->side)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, ctx->ev_filled[slot], 0)) != cudaSuccess)
+                return cuda_fail(ctx, e, "split sweep: join");
+            if ((e = ctx->fns->split_sweep(C, d, 1, A, K, s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "riemann kernel");
+            if ((e = cudaEventRecord(ctx->ev_read[slot], s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "split sweep: slot record");
+        }
+    }
+    return MFC_OK;
+}
+
 // All directional sweeps of one evaluation of L(qin), after the viscous
 // kernels when some eta_i > 0 (their result is the starting value of the
 // accumulation).  out_kind 0 writes L into rhs; 1 and 2 fuse the RK stage
@@ -336,6 +451,7 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
 // out_kind is 1 or 2, where rhs is not written).
 mfc_status eval_L(mfc_ctx* ctx, const double* qin, double* rhs, int out_kind, const double* qn, double* qout,
                   double a, double b, cudaStream_t s) {
+    if (ctx->side) return eval_L_split(ctx, qin, rhs, out_kind, qn, qout, a, b, s);
     const bool mixed = ctx->mode == mfc::MODE_MIXED;
     float* accf = reinterpret_cast<float*>(ctx->r);
     if (ctx->C.viscous) {
@@ -634,6 +750,14 @@ mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* op
         mfc_destroy(ctx);
         return MFC_ERR_ALLOC;
     }
+    if (ctx->mode == mfc::MODE_DF) {
+        const mfc_status st = create_split(ctx);
+        if (st != MFC_OK) {
+            g_init_error = "creating the split double-float sweep's stream, events or edge-value buffers failed";
+            mfc_destroy(ctx);
+            return st;
+        }
+    }
     if ((e = cudaMemset(ctx->scal, 0, sizeof(DevScalars))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         g_init_error = std::string("initialising scalars: ") + cudaGetErrorString(e);
@@ -653,6 +777,7 @@ mfc_status mfc_destroy(mfc_ctx* ctx) {
                       ctx->vel})
         if (p) cudaFree(p);
     release_host_staging(ctx);
+    destroy_split(ctx);
     if (ctx->scal) cudaFree(ctx->scal);
     delete ctx;
     return MFC_OK;

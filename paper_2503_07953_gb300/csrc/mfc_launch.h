@@ -43,6 +43,12 @@ struct VjpArgs {
     int nseg;             // segments per line
 };
 
+// One chunk of lines of a split double-float sweep (mfc_split.cuh).
+struct SplitChunk {
+    int64_t line0, nl;  // lines [line0, line0 + nl) of the sweep direction
+    double* E;          // the chunk's edge values: 2 N_q slots x (n + 2) cells x nl lines
+};
+
 struct LaunchFns {
     // One directional sweep of L(q); mode is MODE_EXACT for the exact
     // tables and MODE_FAST or MODE_MIXED for the others.
@@ -60,6 +66,9 @@ struct LaunchFns {
     // Exact tables only: the primitive / conservative maps.
     cudaError_t (*prim_to_cons)(const Consts& C, const double* w, double* q, cudaStream_t s);
     cudaError_t (*cons_to_prim)(const Consts& C, const double* q, double* w, int* flag, cudaStream_t s);
+    // MODE_DF tables only: one chunk of a split sweep, phase 0 the
+    // reconstruction into K.E, phase 1 the Riemann solve and update from it.
+    cudaError_t (*split_sweep)(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s);
 };
 
 // Exact tables (MODE_EXACT, built without FMA contraction) and fast tables
@@ -80,6 +89,10 @@ cudaError_t sweep_df_nf1(const Consts& C, int dir, int mode, SweepArgs A, cudaSt
 cudaError_t sweep_df_nf2(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
 cudaError_t sweep_df_nf3(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
 cudaError_t sweep_df_nf4(const Consts& C, int dir, int mode, SweepArgs A, cudaStream_t s);
+cudaError_t split_df_nf1(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s);
+cudaError_t split_df_nf2(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s);
+cudaError_t split_df_nf3(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s);
+cudaError_t split_df_nf4(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s);
 
 // Cells per thread along a sweep of `n` cells with `nlines` lines.
 int sweep_segment(int64_t n, int64_t nlines);

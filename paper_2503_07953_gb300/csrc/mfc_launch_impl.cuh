@@ -7,6 +7,7 @@
 
 #include "mfc_fwd.cuh"
 #include "mfc_launch.h"
+#include "mfc_split.cuh"
 #include "mfc_visc.cuh"
 #include "mfc_vjp.cuh"
 
@@ -131,6 +132,38 @@ cudaError_t sweep_df(const Consts& C, int dir, int, SweepArgs A, cudaStream_t s)
         case 1: return sweep_df_nd<NF, 1>(C, dir, A, s);
         case 2: return sweep_df_nd<NF, 2>(C, dir, A, s);
         default: return sweep_df_nd<NF, 3>(C, dir, A, s);
+    }
+}
+
+// One chunk of a split MODE_DF sweep (mfc_split.cuh); the segments are
+// those of the whole direction, so both phases cut the lines alike.
+template <int NF, int ND>
+cudaError_t split_df_nd(const Consts& C, int dir, int phase, SweepArgs A, const SplitChunk& K, cudaStream_t s) {
+    const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];
+    A.seg = sweep_segment(C.n[dir], nlines);
+    A.nseg = (int)((C.n[dir] + A.seg - 1) / A.seg);
+    const int64_t threads = K.nl * A.nseg;
+    if (threads == 0) return cudaSuccess;
+    const unsigned grid = grid_for(threads, kSweepBlock);
+    auto go = [&](auto dirc) {
+        constexpr int D = decltype(dirc)::value;
+        if (phase == 0)
+            recon_kernel_df<NF, ND, D><<<grid, kSweepBlock, 0, s>>>(C, A, K);
+        else
+            riemann_kernel_df<NF, ND, D><<<grid, kSweepBlock, 0, s>>>(C, A, K);
+    };
+    if (dir == 0) go(std::integral_constant<int, 0>());
+    if constexpr (ND >= 2) if (dir == 1) go(std::integral_constant<int, 1>());
+    if constexpr (ND >= 3) if (dir == 2) go(std::integral_constant<int, 2>());
+    return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t split_df(const Consts& C, int dir, int phase, SweepArgs A, SplitChunk K, cudaStream_t s) {
+    switch (C.nd) {
+        case 1: return split_df_nd<NF, 1>(C, dir, phase, A, K, s);
+        case 2: return split_df_nd<NF, 2>(C, dir, phase, A, K, s);
+        default: return split_df_nd<NF, 3>(C, dir, phase, A, K, s);
     }
 }
 

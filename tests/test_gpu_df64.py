@@ -17,6 +17,7 @@ error on the same input (the ratio of the two significands' rounding,
 2^-49 / 2^-53), whichever is larger."""
 import numpy as np
 import pytest
+import torch
 
 from paper_2503_07953_gb300 import workloads as wl
 from tests.helpers import case_errors, oracle_problem, solver_for, to_host
@@ -176,3 +177,32 @@ def test_df64_indicator_overflow_reported(mfc_lib, cuda_device):
         S.check()
     assert ei.value.status == mfc_lib.MFC_ERR_NONPHYSICAL
     S.check()  # the flag was cleared
+
+
+@pytest.mark.parametrize("make", [lambda: wl.shock_bubble_3d(dims=(40, 36, 30)),
+                                  lambda: wl.bubble_collapse_2d(dims=(64, 48)),
+                                  lambda: wl.water_air_shock_tube(300)])
+def test_df64_split_sweeps_equal_fused(mfc_lib, cuda_device, make):
+    """A context runs the MFC_DF64 sweeps split into reconstruction and
+    Riemann kernels on two streams, in chunks of lines; the allocation-free
+    step runs the fused sweep.  The same operations on the same values, up to
+    the compiler's fused multiply-add contraction of the update, which
+    differs between the kernels: after two CFL steps the states agree to
+    1e-13 per field and the first step's dt bit for bit."""
+    from tests.test_zz_no_alloc import descriptors
+    case, W = make()
+    S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+    q_split = S.prim_to_cons(S.from_interior(W))
+    q_fused = q_split.clone()
+    g, e, o = descriptors(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+    stream = torch.cuda.current_stream().cuda_stream
+    dts = torch.zeros(4, dtype=torch.float64, device=cuda_device)
+    for call in range(2):
+        S.rk3_step(q_split, 0.0, dts[2 * call:2 * call + 1])
+        mfc_lib.mfc_rk3_step_noalloc(g, e, o, q_fused.data_ptr(), 0.0, dts[2 * call + 1:2 * call + 2].data_ptr(),
+                                     stream)
+    S.check()
+    d = dts.cpu().numpy()
+    assert d[0] == d[1] and d[2] == pytest.approx(d[3], rel=1e-14)
+    err = case_errors(case, to_host(S, q_split), to_host(S, q_fused))
+    assert (err <= 1e-13).all(), err
