@@ -171,7 +171,13 @@ typedef struct {
 typedef struct mfc_ctx mfc_ctx;
 
 /* Validate the description, derive the constants and allocate the scratch
- * (three state-sized float64 buffers) on the current CUDA device.
+ * (three state-sized float64 buffers) on the current CUDA device.  An
+ * MFC_DF64 context also creates a second CUDA stream, six events and three
+ * edge-value buffers of 2 N_q (n_d + 2) x (lines per chunk) doubles (about
+ * 0.2 of a state buffer each at 256^3): its sweeps run split into a
+ * reconstruction kernel on that stream and a Riemann kernel on the caller's
+ * stream, joined by events, so the calls stay ordered on the caller's stream
+ * and can be captured in a CUDA graph.
  * *out receives the context (NULL on failure). */
 mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts, mfc_ctx** out);
 

@@ -341,15 +341,16 @@ mfc_status eval_dt(mfc_ctx* ctx, const double* q, double dt, cudaStream_t s) {
 
 constexpr int kSplitSlots = 3;
 
-// Lines per chunk of a split sweep along `dir`: enough chunks that the
-// reconstruction of one runs beside the Riemann solve of another, each
-// chunk about two 128-thread blocks per SM of either kernel.
+// Lines per chunk of a split sweep along `dir`: chunks of about four
+// 128-thread blocks per SM of either kernel (measured on the 256^3
+// shock-bubble: 158.6 M cell-updates/s; 151.6 M with two blocks per SM and
+// 107.8 M with one, where chunks are smaller and more of their tails show).
 int64_t split_chunk_lines(const mfc::Consts& C, int dir) {
     const int64_t n = C.n[dir];
     const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / n;
     const int64_t seg = mfc::sweep_segment(n, nlines);
     const int64_t nseg = (n + seg - 1) / seg;
-    int64_t chunks = nlines * nseg / (152LL * 128 * 2);
+    int64_t chunks = nlines * nseg / (152LL * 128 * 4);
     if (chunks < 1) chunks = 1;
     if (chunks > 16) chunks = 16;
     return (nlines + chunks - 1) / chunks;

@@ -2,14 +2,14 @@
 // every cell of a chunk of lines both WENO5 edge values (double-float
 // arithmetic on the float32 pipes, float64 c2p); riemann_kernel_df takes
 // them from the scratch, solves one HLLC problem per face (float64) and
-// finishes the cells as sweep_body does.  Launched on two streams in chunks
-// of lines, the reconstruction of one chunk runs beside the Riemann solve
-// of the previous one, and blocks of both kernels share each SM: the
-// float32 and float64 pipes work at once, where the fused sweep alternates
-// between the two phases within each warp.  The operations are those of
-// sweep_body<MODE_DF> on the same values; only the compiler's fused
-// multiply-add contraction of the update may differ, so the two agree to
-// rounding.
+// finishes the cells as sweep_body does.  Each kernel needs about 155
+// registers where the fused sweep needs 250, so three blocks per SM fit
+// instead of two; launched on two streams in chunks of lines, the
+// reconstruction of one chunk also runs beside the Riemann solve of the
+// previous one, and blocks of both kernels share the SMs.  The operations
+// are those of sweep_body<MODE_DF> on the same values; only the compiler's
+// fused multiply-add contraction of the update may differ, so the two agree
+// to rounding.
 #pragma once
 
 #include "mfc_device.cuh"
