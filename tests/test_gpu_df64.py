@@ -206,3 +206,54 @@ def test_df64_split_sweeps_equal_fused(mfc_lib, cuda_device, make):
     assert d[0] == d[1] and d[2] == pytest.approx(d[3], rel=1e-14)
     err = case_errors(case, to_host(S, q_split), to_host(S, q_fused))
     assert (err <= 1e-13).all(), err
+
+
+@pytest.mark.parametrize("name", ["taylor_green_3d", "walled_2d_nf2", "walled_3d_nf3"])
+def test_df64_viscous(oracle_lib, mfc_lib, cuda_device, name):
+    """With viscous stress the split sweeps accumulate onto the viscous
+    right-hand side (float64, MODE_FAST arithmetic): one evaluation of L
+    against the oracle at FAST's own rounding, and 20 steps of a walled
+    three-fluid run within 1e-11."""
+    from tests.test_gpu_viscous import CASES as VCASES
+    case, W = VCASES[name]()
+    err, err_fast = rhs_errors(oracle_lib, mfc_lib, case, W)
+    assert (err <= np.maximum(TOL, 16 * err_fast)).all(), (err, err_fast)
+    if name == "walled_3d_nf3":
+        P = oracle_problem(oracle_lib, case)
+        S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+        q_o = oracle_lib.prim_to_cons(P, W)
+        q_end, dts = oracle_lib.rk3_run(P, q_o, 20, cfl=case.cfl)
+        q_g = S.from_interior(q_o)
+        for dt in dts:
+            S.rk3_step(q_g, float(dt))
+        S.check()
+        err = case_errors(case, to_host(S, q_g), q_end)
+        assert (err <= TOL).all(), err
+
+
+def test_df64_graph_capture(mfc_lib, cuda_device):
+    """A 192^3 shock-bubble (two chunks per direction, so the ring of edge
+    value slots wraps within each evaluation of L): five steps captured in
+    one CUDA graph, the reconstruction stream forked and joined inside the
+    capture, replay equal bit for bit to the same steps run eagerly."""
+    case, W = wl.shock_bubble_3d(192)
+    S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+    q0 = S.prim_to_cons(S.from_interior(W))
+    q = q0.clone()
+    S.rk3_run(q, 5, 0.0)
+    S.check()
+    qg = q0.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        S.rk3_run(qg, 1, 0.0)
+    torch.cuda.current_stream().wait_stream(side)
+    qg.copy_(q0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.rk3_run(qg, 5, 0.0)
+    qg.copy_(q0)
+    g.replay()
+    torch.cuda.synchronize()
+    S.check()
+    assert torch.equal(qg, q)
