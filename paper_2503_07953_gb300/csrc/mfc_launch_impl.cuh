@@ -109,9 +109,9 @@ cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream
     return cudaGetLastError();
 }
 
-// MODE_DF sweeps: the per-thread march in every direction and on every
-// grid (its float64 share is what bounds it, and the march keeps that
-// share smallest).
+// Fused MODE_DF sweeps, used by the allocation-free step (contexts run the
+// split sweeps of mfc_split.cuh): the per-thread march in every direction
+// and on every grid.
 template <int NF, int ND>
 cudaError_t sweep_df_nd(const Consts& C, int dir, SweepArgs A, cudaStream_t s) {
     const int64_t nlines = C.n[0] * C.n[1] * C.n[2] / C.n[dir];
