@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -55,14 +56,23 @@ SWEEP_SOURCES = ["mfc_df64.cuh", "mfc_device.cuh", "mfc_fwd.cuh", "mfc_split.cuh
     [f"mfc_nf{n}_{m}.cu" for n in (1, 2, 3, 4) for m in ("exact", "fast", "df")]
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments, whitespace runs collapsed (the sweep
+    sources hold no string literal with a comment marker)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_fingerprint() -> str:
-    """Hash of the forward sweep kernels' sources and flags (no machine):
-    identifies the code an ncu capture of those kernels was taken on."""
+    """Hash of the forward sweep kernels' code (comments and layout
+    ignored) and flags, no machine: identifies the code an ncu capture of
+    those kernels was taken on."""
     h = hashlib.sha256()
     for name in SWEEP_SOURCES:
         h.update(name.encode())
-        with open(os.path.join(CSRC, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(CSRC, name), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     flags = [f for f in ARCH + NVCC_FLAGS if f not in (INCLUDE, CSRC)]  # no machine paths
     h.update(" ".join(flags).encode())
     h.update(repr(sorted(PER_SOURCE_FLAGS.items())).encode())
