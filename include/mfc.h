@@ -85,12 +85,15 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   pipes, which on GB300 run 64 times as many operations per clock as the
  *   float64 pipe.  Everything else (conservative-to-primitive conversion,
  *   HLLC, flux differences, stage update, CFL reduction) is the
- *   MFC_FP64_FAST float64 arithmetic, so the two pipes work concurrently.
- *   Agrees with MFC_FP64 to rounding (the same 1e-11 bar as MFC_FP64_FAST).
- *   Primitive values must keep the smoothness indicators inside the
- *   float32 range (differences across a stencil below ~1e18); an overflow
- *   is reported as MFC_ERR_NONPHYSICAL.  The adjoint entry points of an MFC_DF64 context
- *   run in the MFC_FP64_FAST arithmetic. */
+ *   MFC_FP64_FAST float64 arithmetic.  The reconstruction is carried on
+ *   the stencil's consecutive differences, so constant data reconstruct
+ *   exactly.  Agrees with MFC_FP64 to rounding (the same 1e-11 bar as
+ *   MFC_FP64_FAST).  Primitive values must keep the smoothness indicators
+ *   inside the float32 range (differences across a stencil below ~1e18);
+ *   an overflow is reported as MFC_ERR_NONPHYSICAL.  The adjoint entry
+ *   points of an MFC_DF64 context recompute the RK stages with the
+ *   double-float sweeps and run the adjoint sweeps in the MFC_FP64_FAST
+ *   arithmetic. */
 typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2, MFC_DF64 = 3 } mfc_precision;
 
 /* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2),

@@ -257,3 +257,23 @@ def test_df64_graph_capture(mfc_lib, cuda_device):
     torch.cuda.synchronize()
     S.check()
     assert torch.equal(qg, q)
+
+
+@pytest.mark.parametrize("name", ["smooth_3d_mixed_bc", "stiff_smooth_2d", "smooth_2d_kapila"])
+def test_df64_rk3_step_vjp_dot_product(oracle_lib, mfc_lib, cuda_device, name):
+    """The adjoint step of a double-float context recomputes the RK stages
+    with the double-float sweeps and runs the adjoint sweeps in float64
+    (MFC_FP64_FAST arithmetic): <v, J w> from the oracle's dual numbers
+    against <J^T v, w> from the library, 1e-10 as for MFC_FP64_FAST."""
+    from tests.test_gpu_adjoint import CASES as ACASES, directions, dot
+    case, W = ACASES[name]()
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+    q = oracle_lib.prim_to_cons(P, W)
+    dt = oracle_lib.cfl_dt(P, q, case.cfl)
+    w, v = directions(case, q, 8)
+    _, Jw = oracle_lib.rk3_step_jvp(P, q, w, dt)
+    qb = S.rk3_step_vjp(S.from_interior(q), dt, S.from_interior(v))
+    lhs = dot(v, Jw)
+    rhs = dot(to_host(S, qb), w)
+    assert rhs == pytest.approx(lhs, rel=1e-10), (lhs, rhs)
