@@ -69,6 +69,7 @@ def _desc(mfc_lib, **over):
     ({"x": ("e", ("gamma", 1), 1.0)}, "gamma"),
     ({"x": ("e", ("pi_inf", 0), -1.0)}, "pi_inf"),
     ({"x": ("o", "precision", 7)}, "precision"),
+    ({"x": ("o", "precision", 4)}, "precision"),
     ({"x": ("o", "weno", 4)}, "WENO"),
     ({"x": ("o", "weno", 3), "y": ("o", "teno_ct", 1.5)}, "teno_ct"),
     ({"x": ("o", "weno_eps", 0.0)}, "weno_eps"),
@@ -88,6 +89,21 @@ def test_invalid_descriptions_rejected_on_host(mfc_lib, case, why):
         mfc_lib.mfc_init(g, e, o)
     assert ei.value.status == mfc_lib.MFC_ERR_ARG
     assert why in mfc_lib.mfc_last_error(None)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_every_precision_passes_the_host_checks(mfc_lib, precision):
+    """MFC_FP64, MFC_MIXED, MFC_FP64_FAST and MFC_DF64 are valid: mfc_init
+    gets past the host-side checks (without a GPU it then fails on the
+    device with MFC_ERR_CUDA; with one it returns a context)."""
+    g, e, o = _desc(mfc_lib)
+    o.precision = precision
+    try:
+        ctx = mfc_lib.mfc_init(g, e, o)
+    except mfc_lib.MfcError as err:
+        assert err.status != mfc_lib.MFC_ERR_ARG, mfc_lib.mfc_last_error(None)
+    else:
+        mfc_lib.mfc_destroy(ctx)
 
 
 def test_null_context_is_an_argument_error(mfc_lib):
