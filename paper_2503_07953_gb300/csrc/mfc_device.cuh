@@ -606,8 +606,98 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
     return out;
 }
 
+// MODE_FAST WENO5 of one cell (JS, mapped and Z weights), arranged for few
+// float64 operations.  With the consecutive differences D_j = f_{j+1} - f_j
+// of the stencil, substencil r has the second difference a_r (a_0 = D12 -
+// D01, a_1 = D23 - D12, a_2 = D34 - D23) and the first difference g_r
+// (g_0 = 3 D12 - D01, g_1 = D12 + D23, g_2 = D34 - 3 D23), and the k = 3
+// candidate polynomials and smoothness indicators of Sec. 4.2.2 become
+//   4 beta_r = (13/3) a_r^2 + g_r^2,
+//   12 (right-edge candidate_r - f2) = a_r + 3 s_r g_r,   s = (+1, +1, -1),
+//   12 (left-edge candidate_r - f2)  = a_r - 3 s_r g_r.
+// The weights depend only on ratios of eps + beta_r, so they are evaluated
+// on t_r = 4 (eps + beta_r).  Each edge value is f2 + sum_r omega_r
+// (candidate_r - f2), so constant data reconstruct exactly and the rounding
+// of the weights only touches the correction.  Unnormalised weights: JS
+// alpha_r = d_r prod_{s != r} t_s^2 (alpha_r = d_r / t_r^2 times the product
+// of all t_s^2); mapped (Henrick 2005) g(w) = w (d + d^2 + w (w - 3 d)) /
+// (d^2 + w (1 - 2 d)) of the normalised JS weights w, as numerator times the
+// other two stencils' denominators; Z d_r (t_r + tau) prod_{s != r} t_s.
+// The mapped weights of the two edges sum to within [5e-6, 3] each, so their
+// normalisations share one reciprocal.
+__device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f2, double f3, double f4, int variant,
+                                                  double eps, double& vl, double& vr) {
+    const double D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
+    const double a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const double g[3] = {fma(3.0, D12, -D01), D12 + D23, fma(-3.0, D23, D34)};
+    const double e4 = 4.0 * eps;
+    double t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = fma(g[r], g[r], fma((13.0 / 3.0) * a[r], a[r], e4));
+    const double cR[3] = {fma(3.0, g[0], a[0]), fma(3.0, g[1], a[1]), fma(-3.0, g[2], a[2])};
+    const double cL[3] = {fma(-3.0, g[0], a[0]), fma(-3.0, g[1], a[1]), fma(3.0, g[2], a[2])};
+    double wR[3], wL[3], nR, nL;
+    if (variant == WENO_Z) {
+        const double tau = fabs(t[0] - t[2]);
+        const double P0 = (t[0] + tau) * (t[1] * t[2]), P1 = (t[1] + tau) * (t[0] * t[2]);
+        const double P2 = (t[2] + tau) * (t[0] * t[1]);
+        const double m1 = 0.6 * P1;
+        wR[0] = 0.1 * P0, wR[1] = m1, wR[2] = 0.3 * P2;
+        wL[0] = 0.3 * P0, wL[1] = m1, wL[2] = 0.1 * P2;
+    } else {
+        const double s0 = t[0] * t[0], s1 = t[1] * t[1], s2 = t[2] * t[2];
+        const double P0 = s1 * s2, P1 = s0 * s2, P2 = s0 * s1;
+        const double m1 = 0.6 * P1;
+        wR[0] = 0.1 * P0, wR[1] = m1, wR[2] = 0.3 * P2;
+        wL[0] = 0.3 * P0, wL[1] = m1, wL[2] = 0.1 * P2;
+    }
+    nR = (wR[0] + wR[1]) + wR[2];
+    nL = (wL[0] + wL[1]) + wL[2];
+    double iR, iL;
+    if (variant == WENO_M) {
+        const double dR[3] = {0.1, 0.6, 0.3}, dL[3] = {0.3, 0.6, 0.1};
+        double* ws[2] = {wR, wL};
+        double* ns[2] = {&nR, &nL};
+        const double* ds[2] = {dR, dL};
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            double* w = ws[side];
+            const double* d = ds[side];
+            const double inv = rcp_nr(*ns[side]);
+            double N[3], D[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double x = w[r] * inv;
+                N[r] = x * fma(x, x - 3.0 * d[r], d[r] * (1.0 + d[r]));
+                D[r] = fma(x, 1.0 - 2.0 * d[r], d[r] * d[r]);
+            }
+            w[0] = N[0] * (D[1] * D[2]);
+            w[1] = N[1] * (D[0] * D[2]);
+            w[2] = N[2] * (D[0] * D[1]);
+            *ns[side] = (w[0] + w[1]) + w[2];
+        }
+        // 1 / (12 nR nL): nL / (12 nR nL) = 1 / (12 nR) and nR / (12 nR nL) = 1 / (12 nL)
+        const double r = rcp_nr((12.0 * nR) * nL);
+        iR = nL * r;
+        iL = nR * r;
+    } else {
+        iR = rcp_nr(12.0 * nR);
+        iL = rcp_nr(12.0 * nL);
+    }
+    const double sR = fma(wR[2], cR[2], fma(wR[1], cR[1], wR[0] * cR[0]));
+    const double sL = fma(wL[2], cL[2], fma(wL[1], cL[1], wL[0] * cL[0]));
+    vr = fma(iR, sR, f2);
+    vl = fma(iL, sL, f2);
+}
+
 template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int variant, R eps, R ct, R& vl, R& vr) {
+    if constexpr (MODE == MODE_FAST) {
+        if (variant != WENO_TENO) {
+            weno5_cell_fast64(f0, f1, f2, f3, f4, variant, eps, vl, vr);
+            return;
+        }
+    }
     if constexpr (MODE == MODE_EXACT) {
         const double c13 = 13.0 / 12.0, c14 = 0.25;
         double beta[3];
@@ -791,29 +881,35 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
     const R SK = left ? SL : SR;
     const bool star = left ? (SL < R(0)) : (SR > R(0));
 
-#pragma unroll
-    for (int i = 0; i < NF; ++i) F[i] = w[i] * uK;
-#pragma unroll
-    for (int e = 0; e < ND; ++e) {
-        F[L::MOM + e] = rK * uK * w[L::MOM + e];
-        if (e == DIR) F[L::MOM + e] = F[L::MOM + e] + pK;
-    }
-    F[L::E] = (EK + pK) * uK;
-    if (star) {
-        const R chi = A::quot(SK - uK, SK - Ss);
-#pragma unroll
-        for (int i = 0; i < NF; ++i) {
-            const R Us = chi * w[i];
-            F[i] = F[i] + SK * (Us - w[i]);
+    if constexpr (MODE != MODE_EXACT) {
+        // The same star-state fluxes with one reciprocal.  With
+        // B = S_K - S*, chi = (S_K - u_K)/B and dl = S_K (chi - 1) =
+        // S_K (S* - u_K)/B (= chi S* - u_K):
+        //   F*_K = F_K + S_K (U*_K - U_K) is (u_K + dl) U_K for the partial
+        //   densities and the tangential momenta, p_K + rho_K (u_K^2 + S_K dl)
+        //   for the normal momentum, and for the energy
+        //   E*_K = chi rho_K (E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))))
+        //        = ((S_K - u_K)(E_K + rho_K (S* - u_K) S*) + (S* - u_K) p_K) / B.
+        R m = uK, Fn, FE;
+        if (star) {
+            const R du = Ss - uK;
+            const R iB = rcp<R>(SK - Ss);
+            const R dl = SK * du * iB;
+            m = uK + dl;
+            Fn = fma(rK, fma(uK, uK, SK * dl), pK);
+            const R Es = fma(du, pK, (SK - uK) * fma(rK * du, Ss, EK)) * iB;
+            FE = fma(SK, Es - EK, (EK + pK) * uK);
+        } else {
+            Fn = fma(rK * uK, uK, pK);
+            FE = (EK + pK) * uK;
         }
 #pragma unroll
-        for (int e = 0; e < ND; ++e) {
-            const R Us = chi * rK * (e == DIR ? Ss : w[L::MOM + e]);
-            F[L::MOM + e] = F[L::MOM + e] + SK * (Us - rK * w[L::MOM + e]);
-        }
-        const R Es = chi * rK * (A::quot(EK, rK) + (Ss - uK) * (Ss + A::quot(pK, rK * (SK - uK))));
-        F[L::E] = F[L::E] + SK * (Es - EK);
-        if (C.low_mach == 2) {
+        for (int i = 0; i < NF; ++i) F[i] = w[i] * m;
+        const R rm = rK * m;
+#pragma unroll
+        for (int e = 0; e < ND; ++e) F[L::MOM + e] = (e == DIR) ? Fn : rm * w[L::MOM + e];
+        F[L::E] = FE;
+        if (star && C.low_mach == 2) {
             // anti-dissipation pressure correction (Sec. 4.2.4)
             const R pd = A::quot(rho[0] * rho[1] * (SL - un[0]) * (SR - un[1]) * (un[1] - un[0]),
                                  rho[1] * (SR - un[1]) - rho[0] * (SL - un[0]));
@@ -821,12 +917,47 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
             F[UN] = F[UN] + apc;
             F[L::E] = F[L::E] + apc * Ss;
         }
-        uf = Ss;
-    } else {
-        uf = uK;
-    }
+        uf = star ? Ss : uK;
 #pragma unroll
-    for (int j = 0; j < NF - 1; ++j) F[L::A + j] = w[L::A + j] * uf;
+        for (int j = 0; j < NF - 1; ++j) F[L::A + j] = w[L::A + j] * uf;
+    } else {
+#pragma unroll
+        for (int i = 0; i < NF; ++i) F[i] = w[i] * uK;
+#pragma unroll
+        for (int e = 0; e < ND; ++e) {
+            F[L::MOM + e] = rK * uK * w[L::MOM + e];
+            if (e == DIR) F[L::MOM + e] = F[L::MOM + e] + pK;
+        }
+        F[L::E] = (EK + pK) * uK;
+        if (star) {
+            const R chi = A::quot(SK - uK, SK - Ss);
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                const R Us = chi * w[i];
+                F[i] = F[i] + SK * (Us - w[i]);
+            }
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                const R Us = chi * rK * (e == DIR ? Ss : w[L::MOM + e]);
+                F[L::MOM + e] = F[L::MOM + e] + SK * (Us - rK * w[L::MOM + e]);
+            }
+            const R Es = chi * rK * (A::quot(EK, rK) + (Ss - uK) * (Ss + A::quot(pK, rK * (SK - uK))));
+            F[L::E] = F[L::E] + SK * (Es - EK);
+            if (C.low_mach == 2) {
+                // anti-dissipation pressure correction (Sec. 4.2.4)
+                const R pd = A::quot(rho[0] * rho[1] * (SL - un[0]) * (SR - un[1]) * (un[1] - un[0]),
+                                     rho[1] * (SR - un[1]) - rho[0] * (SL - un[0]));
+                const R apc = (zlm - R(1)) * pd;
+                F[UN] = F[UN] + apc;
+                F[L::E] = F[L::E] + apc * Ss;
+            }
+            uf = Ss;
+        } else {
+            uf = uK;
+        }
+#pragma unroll
+        for (int j = 0; j < NF - 1; ++j) F[L::A + j] = w[L::A + j] * uf;
+    }
 }
 
 // Index of the interior cell that supplies the value of cell c along an
