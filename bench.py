@@ -198,59 +198,107 @@ def field_errors(a: torch.Tensor, b: torch.Tensor, nf: int, nd: int):
     return [(a[k] - b[k]).abs().max().item() / den[k] if den[k] > 0 else 0.0 for k in range(b.shape[0])]
 
 
-def cpu_baseline_leg(workload: str, sample_n: int, steps: int) -> dict:
-    """The oracle, as it stands, on a bounded sample of the same workload."""
-    import oracle
-    oracle.build()
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def sample_case(workload: str, sample_n: int):
     if workload == "shock_bubble_3d":
-        case, W = wl.shock_bubble_3d(dims=(sample_n,) * 3)
-    elif workload == "random_interfaces_3d":
-        case, W = wl.random_interfaces_3d(dims=(sample_n,) * 3)
-    elif workload == "bubble_collapse_2d":
-        case, W = wl.bubble_collapse_2d(dims=(sample_n * 8, sample_n * 8))
-    else:
-        case, W = wl.water_air_shock_tube(1000)
-    P = oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
-                       bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
-    q = oracle.prim_to_cons(P, W)
-    t0 = time.perf_counter()
-    q, dts = oracle.rk3_run(P, q, steps, cfl=case.cfl)
-    el = time.perf_counter() - t0
-    cells = case.ncells
-    return {"value": cells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{case.name} {'x'.join(map(str, case.n))} cells, {steps} RK3 steps "
-                      f"(CFL dt each step), single-threaded, {el:.1f} s"}
+        return wl.shock_bubble_3d(dims=(sample_n,) * 3)
+    if workload == "random_interfaces_3d":
+        return wl.random_interfaces_3d(dims=(sample_n,) * 3)
+    if workload == "bubble_collapse_2d":
+        return wl.bubble_collapse_2d(dims=(sample_n * 8, sample_n * 8))
+    return wl.water_air_shock_tube(1000)
+
+
+def time_oracle(workload: str, sample_n: int, steps: int, parallel: bool) -> dict:
+    """The oracle, as it stands, on `steps` RK3 steps of a bounded sample of
+    the workload: single-threaded, or its OpenMP build on all host cores."""
+    import oracle
+    oracle.build(openmp=parallel)
+    oracle.set_parallel(parallel)
+    try:
+        case, W = sample_case(workload, sample_n)
+        P = oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
+                           bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
+        q = oracle.prim_to_cons(P, W)
+        threads = oracle.threads()
+        t0 = time.perf_counter()
+        q, dts = oracle.rk3_run(P, q, steps, cfl=case.cfl)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_parallel(False)
+    how = "single-threaded" if threads == 1 else f"OpenMP over the grid lines on {threads} threads"
+    return {"value": case.ncells * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{case.name} {'x'.join(map(str, case.n))} cells, {steps} RK3 steps (CFL dt each step), "
+                      f"{how}, {el:.1f} s"}
+
+
+def cpu_baseline_leg(workload: str, ndim: int) -> dict:
+    """The oracle on all host cores (its OpenMP build) on a bounded sample,
+    with the single-threaded oracle beside it; nproc and the CPU model."""
+    three_d = ndim == 3
+    single = time_oracle(workload, 64 if three_d else 0, 5 if three_d else 50, parallel=False)
+    allc = time_oracle(workload, 128 if three_d else 0, 3 if three_d else 50, parallel=True)
+    out = dict(allc)
+    out["nproc"] = os.cpu_count()
+    out["cpu_model"] = cpu_model()
+    out["single_thread"] = single
+    out["parallel_speedup"] = allc["value"] / single["value"]
+    return out
 
 
 def run_reference(args, world, rank):
-    """The reference arm: the plain CPU oracle, timed on the host cores."""
+    """The reference arm: the plain CPU oracle (its OpenMP build, all host
+    cores), timed on a bounded sample of the workload."""
     if rank != 0:
         return
     import oracle
-    oracle.build()
-    sample_n = 40
+    oracle.build(openmp=True)
+    oracle.set_parallel(True)
     if args.workload == "shock_bubble_3d":
-        case, W = wl.shock_bubble_3d(dims=(sample_n,) * 3)
+        case, W = wl.shock_bubble_3d(dims=(64,) * 3)
     elif args.workload == "random_interfaces_3d":
-        case, W = wl.random_interfaces_3d(dims=(sample_n,) * 3)
+        case, W = wl.random_interfaces_3d(dims=(48,) * 3)
     elif args.workload == "bubble_collapse_2d":
         case, W = wl.bubble_collapse_2d(dims=(256, 256))
     else:
         case, W = wl.water_air_shock_tube(1000)
     P = oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
                        bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
+    threads = oracle.threads()
     q = oracle.prim_to_cons(P, W)
     q, _ = oracle.rk3_run(P, q, args.warmup, cfl=case.cfl)
     t0 = time.perf_counter()
     q, _ = oracle.rk3_run(P, q, args.steps, cfl=case.cfl)
     el = time.perf_counter() - t0
+    oracle.set_parallel(False)
     value = case.ncells * args.steps / el
-    sample = f"{case.name} {'x'.join(map(str, case.n))} cells per step (bounded sample of the workload), single-threaded"
+    sample = (f"{case.name} {'x'.join(map(str, case.n))} cells per step (bounded sample of the workload), "
+              f"OpenMP over the grid lines on {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": describe(make_workload_stub(args)), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -447,8 +495,7 @@ def run_ours(args, world, rank, local):
                          "precision": args.precision}
         torch.cuda.empty_cache()
         line.update(extras)
-        sample_n = 64 if case.ndim == 3 else 0
-        line["cpu_baseline"] = cpu_baseline_leg(args.workload, sample_n, 5 if case.ndim == 3 else 50)
+        line["cpu_baseline"] = cpu_baseline_leg(args.workload, case.ndim)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -24,26 +24,46 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mfc_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+# the same source built with OpenMP: the loops over grid lines and cells run
+# on all host cores (used to time the CPU baseline; results are identical)
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
 WENO_JS, WENO_M, WENO_Z, WENO_TENO = 0, 1, 2, 3
 MAXF = 4
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_parallel = False
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no FMA contraction, no fast-math)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction, no fast-math);
+    openmp=True builds the multi-threaded copy."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           _SRC, "-o", tmp]
+    so = _SO_OMP if openmp else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(_SRC):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    if openmp:
+        cmd.append("-fopenmp")
+    cmd += [_SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def set_parallel(on: bool) -> None:
+    """Route the module's calls to the OpenMP build (True) or to the
+    single-threaded build (False, the default)."""
+    global _parallel
+    _parallel = bool(on)
+
+
+def threads() -> int:
+    """Host threads the current build's loops use."""
+    return int(_load().oc_threads())
 
 
 class _Problem(ctypes.Structure):
@@ -59,14 +79,15 @@ class _Problem(ctypes.Structure):
 
 
 def _load():
-    global _lib
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        key = "omp" if _parallel else "serial"
+        if key not in _libs:
+            lib = ctypes.CDLL(build(openmp=_parallel))
             P = ctypes.POINTER(_Problem)
             dp = ctypes.POINTER(ctypes.c_double)
             i64p = ctypes.POINTER(ctypes.c_int64)
             sig = {
+                "oc_threads": (ctypes.c_int, []),
                 "oc_nfields": (ctypes.c_int, [P]),
                 "oc_prim_to_cons": (ctypes.c_int, [P, dp, dp]),
                 "oc_cons_to_prim": (ctypes.c_int, [P, dp, dp]),
@@ -88,8 +109,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[key] = lib
+    return _libs[key]
 
 
 @dataclass

@@ -1,5 +1,5 @@
 /*
- * Plain, slow, single-threaded FP64 CPU oracle for the five-equation
+ * Plain, slow FP64 CPU oracle for the five-equation
  * WENO5 / HLLC / TVD-RK3 finite-volume method of arXiv 2503.07953 (MFC 5.0).
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
@@ -7,6 +7,11 @@
  * product path (the CUDA library and its Python binding) never imports,
  * links or calls it, and this file shares no code, header, table or helper
  * with that path.
+ *
+ * Built twice from this one file: single-threaded (the tests), and with
+ * OpenMP for the timing of the CPU baseline, where the loops over grid lines
+ * and cells run on all host cores.  Each cell's arithmetic is the same in
+ * both builds, so their results are identical bit for bit.
  *
  * Every numerical routine is templated on its scalar type:
  *   double  - the oracle proper;
@@ -55,6 +60,9 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -202,13 +210,18 @@ struct Eos {
 
 int g_bad = 0; /* count of non-physical states met (rho <= 0 or c^2 <= 0 / NaN) */
 
+inline void note_bad() {
+#pragma omp atomic
+    g_bad++;
+}
+
 /* Conservative -> primitive (a2): rho = sum alpha_i rho_i, u = (rho u)/rho,
  * p = (rho E - 1/2 rho |u|^2 - Pi)/Gamma. */
 template <class T>
 void cons_to_prim(const Lay& L, const Eos& eos, const T* q, T* w) {
     T rho = q[L.rho(0)];
     for (int i = 1; i < L.nf; ++i) rho = rho + q[L.rho(i)];
-    if (!(val(rho) > 0.0)) g_bad++;
+    if (!(val(rho) > 0.0)) note_bad();
     for (int i = 0; i < L.nf; ++i) w[L.rho(i)] = q[L.rho(i)];
     T u2 = T(0.0);
     for (int d = 0; d < L.nd; ++d) {
@@ -245,7 +258,7 @@ void prim_to_cons(const Lay& L, const Eos& eos, const T* w, T* q) {
  * fluid it is the phasic c_i of Sec. 2.1.1). */
 template <class T> T sound_speed(T rho, T p, T Gamma, T Pi) {
     T c2 = ((Gamma + T(1.0)) * p + Pi) / (Gamma * rho);
-    if (!(val(c2) > 0.0)) g_bad++;
+    if (!(val(c2) > 0.0)) note_bad();
     return sqrt(c2);
 }
 
@@ -277,7 +290,7 @@ template <class T> T wood_c2(const Eos& eos, T rho, T p, T a1) {
 template <class T> T model_sound_speed(const Lay& L, const Eos& eos, const T* w, T rho, T Gamma, T Pi) {
     if (eos.model == 0) return sound_speed(rho, w[L.E()], Gamma, Pi);
     T c2 = wood_c2(eos, rho, w[L.E()], w[L.alpha(0)]);
-    if (!(val(c2) > 0.0)) g_bad++;
+    if (!(val(c2) > 0.0)) note_bad();
     return sqrt(c2);
 }
 
@@ -766,42 +779,41 @@ void rhs_full(const oc_problem& P, const T* q, T* Lout) {
     FullView<T> V{&P, q, ncell};
     for (int64_t i = 0; i < (int64_t)nq * ncell; ++i) Lout[i] = T(0.0);
     if (eos.viscous) {
-        for (int k = 0; k < P.n[2]; ++k)
-            for (int j = 0; j < P.n[1]; ++j)
-                for (int i = 0; i < P.n[0]; ++i) {
-                    int c[3] = {i, j, k};
-                    T Vc[MAXQ];
-                    viscous_cell(V, L, eos, c, Vc);
-                    const int64_t cl = lin(P, i, j, k);
-                    for (int f = 0; f < nq; ++f) Lout[f * ncell + cl] = Vc[f];
-                }
+#pragma omp parallel for schedule(static)
+        for (int64_t cl = 0; cl < ncell; ++cl) {
+            int c[3] = {(int)(cl % P.n[0]), (int)((cl / P.n[0]) % P.n[1]), (int)(cl / ((int64_t)P.n[0] * P.n[1]))};
+            T Vc[MAXQ];
+            viscous_cell(V, L, eos, c, Vc);
+            for (int f = 0; f < nq; ++f) Lout[f * ncell + cl] = Vc[f];
+        }
     }
     for (int ax = 0; ax < P.ndim; ++ax) {
         const int n = P.n[ax];
         const double dx = dx_of(P, ax);
-        std::vector<std::array<T, MAXQ>> F(n + 1);
-        std::vector<T> uf(n + 1);
-        /* iterate over the lines along ax */
-        int t1 = (ax == 0) ? 1 : 0, t2 = (ax == 2) ? 1 : 2;
-        for (int b = 0; b < P.n[t2]; ++b)
-            for (int a = 0; a < P.n[t1]; ++a) {
-                int c[3];
-                c[t1] = a;
-                c[t2] = b;
-                for (int s = -1; s < n; ++s) { /* face s+1/2, stored at s+1 */
-                    c[ax] = s;
-                    face_flux(V, L, eos, ax, c, F[s + 1].data(), uf[s + 1]);
-                }
-                for (int s = 0; s < n; ++s) {
-                    c[ax] = s;
-                    int64_t cl = lin(P, c[0], c[1], c[2]);
-                    T qc[MAXQ], t[MAXQ];
-                    V.load(cl, qc);
-                    T Kc = cell_K(L, eos, qc);
-                    cell_term(L, dx, F[s].data(), uf[s], F[s + 1].data(), uf[s + 1], qc, Kc, eos.model == 1, t);
-                    for (int k = 0; k < nq; ++k) Lout[k * ncell + cl] = Lout[k * ncell + cl] + t[k];
-                }
+        /* iterate over the lines along ax (each line writes only its own cells) */
+        const int t1 = (ax == 0) ? 1 : 0, t2 = (ax == 2) ? 1 : 2;
+        const int64_t nlines = (int64_t)P.n[t1] * P.n[t2];
+#pragma omp parallel for schedule(static)
+        for (int64_t line = 0; line < nlines; ++line) {
+            std::vector<std::array<T, MAXQ>> F(n + 1);
+            std::vector<T> uf(n + 1);
+            int c[3];
+            c[t1] = (int)(line % P.n[t1]);
+            c[t2] = (int)(line / P.n[t1]);
+            for (int s = -1; s < n; ++s) { /* face s+1/2, stored at s+1 */
+                c[ax] = s;
+                face_flux(V, L, eos, ax, c, F[s + 1].data(), uf[s + 1]);
             }
+            for (int s = 0; s < n; ++s) {
+                c[ax] = s;
+                int64_t cl = lin(P, c[0], c[1], c[2]);
+                T qc[MAXQ], t[MAXQ];
+                V.load(cl, qc);
+                T Kc = cell_K(L, eos, qc);
+                cell_term(L, dx, F[s].data(), uf[s], F[s + 1].data(), uf[s + 1], qc, Kc, eos.model == 1, t);
+                for (int k = 0; k < nq; ++k) Lout[k * ncell + cl] = Lout[k * ncell + cl] + t[k];
+            }
+        }
     }
 }
 
@@ -843,10 +855,13 @@ template <class T, class RhsFn>
 void rk3_generic(int64_t n, T* q, double dt, RhsFn rhs) {
     std::vector<T> q1(n), q2(n), Lb(n);
     rhs(q, Lb.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) q1[i] = q[i] + T(dt) * Lb[i];
     rhs(q1.data(), Lb.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) q2[i] = T(RK_A2) * q[i] + T(RK_B2) * (q1[i] + T(dt) * Lb[i]);
     rhs(q2.data(), Lb.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) q[i] = T(RK_A3) * q[i] + T(RK_B3) * (q2[i] + T(dt) * Lb[i]);
 }
 
@@ -865,6 +880,8 @@ template <class T> double cfl_dt(const oc_problem& P, const T* q, double cfl) {
     const int64_t ncell = (int64_t)P.n[0] * P.n[1] * P.n[2];
     FullView<T> V{&P, q, ncell};
     double m = INFINITY;
+    /* a minimum: the same value whatever the order of the cells */
+#pragma omp parallel for schedule(static) reduction(min : m)
     for (int64_t c = 0; c < ncell; ++c) {
         T qc[MAXQ], w[MAXQ];
         V.load(c, qc);
@@ -921,6 +938,16 @@ inline int nfields(const oc_problem* P) { return 2 * P->nf + P->ndim; }
 /* C entry points (ctypes)                                             */
 /* ------------------------------------------------------------------ */
 extern "C" {
+
+/* Threads the loops over lines and cells use: 1 in the single-threaded
+ * build, the OpenMP default (all host cores, or OMP_NUM_THREADS) otherwise. */
+int oc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 int oc_nfields(const oc_problem* P) { return check_problem(P) ? -1 : nfields(P); }
 
