@@ -64,7 +64,19 @@ typedef enum {
     MFC_ERR_UNSUPPORTED = -5   /* valid but not supported by this build */
 } mfc_status;
 
-typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2 } mfc_bc;
+/* Boundary conditions (Sec. 3.3): periodic wrap, transmissive (zeroth-order
+ * extrapolation) and reflective (mirror with the normal momentum negated)
+ * are applied by the library; their ghost cells in the caller's buffers are
+ * neither read nor written.  MFC_BC_HALO is the side of a subdomain of a
+ * domain decomposition (the paper's block decomposition with one halo
+ * exchange per Runge-Kutta stage, Sec. 4.3): the ghost cells of that side
+ * hold the neighbouring subdomain's cells, which the caller writes before
+ * every evaluation of L (grid.ghost >= 3), and the library reads them as
+ * cells.  A context with a halo side steps with mfc_rk3_stage, the caller
+ * refreshing the halos of each stage's input; mfc_rk3_step, mfc_rk3_run,
+ * mfc_rk3_step_batch_host, mfc_rk3_step_noalloc and the adjoints return
+ * MFC_ERR_UNSUPPORTED for it, as does mfc_init with viscosity. */
+typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2, MFC_BC_HALO = 3 } mfc_bc;
 
 /* MFC_FP64: everything in float64, every operation in the order of the
  *   defining formula with IEEE division and square root and no fused
@@ -123,9 +135,13 @@ typedef struct {
  * each face by second-order central differences of the cell velocities
  * (normal derivative across the face; tangential derivatives the mean of
  * the two cells' centred differences; face velocity and volume fractions
- * the means of the two cells').  The CFL dt stays the convective one: the
- * explicit viscous limit rho dx^2 / (2 ndim eta) is the caller's to respect
- * (pass dt > 0).  With viscosity the adjoints and mfc_rk3_step_noalloc
+ * the means of the two cells').  The CFL dt is the convective one unless
+ * opts.viscous_dt = 1, which adds the explicit viscous limit (the paper
+ * states none; the usual bound of an explicit step of the momentum
+ * diffusion): dt = CFL min over cells of min(min_d dx_d / (|u_d| + c),
+ * rho min_d dx_d^2 / (2 ndim eta)), eta the cell's mixture viscosity
+ * (cells with eta = 0 have no viscous bound).  Without it, the viscous limit
+ * is the caller's to respect (pass dt > 0).  With viscosity the adjoints and mfc_rk3_step_noalloc
  * return MFC_ERR_UNSUPPORTED.  All eta_i = 0 is the inviscid method, bit
  * for bit. */
 typedef struct {
@@ -169,6 +185,7 @@ typedef struct {
     int32_t model;         /* mfc_model */
     int32_t riemann;       /* mfc_riemann */
     int32_t low_mach;      /* mfc_low_mach */
+    int32_t viscous_dt;    /* 1: the CFL dt also respects the explicit viscous limit (see mfc_eos); 0: convective only */
 } mfc_opts;
 
 typedef struct mfc_ctx mfc_ctx;
@@ -217,6 +234,21 @@ mfc_status mfc_rhs(mfc_ctx* ctx, const double* q, double* rhs, void* stream);
  * device without a host round trip.  dt_used (nullable) is a DEVICE pointer
  * to one double that receives the dt of this step. */
 mfc_status mfc_rk3_step(mfc_ctx* ctx, double* q, double dt, double* dt_used, void* stream);
+
+/* One stage of the TVD-RK3 step (Sec. 3.4) on caller buffers, for callers
+ * that act between the stages (a domain decomposition refreshes the halo
+ * cells of each stage's input, MFC_BC_HALO):
+ *   stage 1: q_out = q_in + dt L(q_in)                       (q_n unused, may be NULL)
+ *   stage 2: q_out = 3/4 q_n + 1/4 (q_in + dt L(q_in))
+ *   stage 3: q_out = 1/3 q_n + 2/3 (q_in + dt L(q_in))
+ * dt > 0 is the step's time step, the same for its three stages (for a
+ * decomposed domain: the minimum over the subdomains of mfc_compute_dt).
+ * The three stages in order, on q_in = q, q1, q2 with q_out = q1, q2, q and
+ * q_n = q, give exactly mfc_rk3_step at that dt.  All pointers are DEVICE
+ * buffers in the context's layout; q_out may alias q_n but not q_in.  Only
+ * interior cells of q_out are written. */
+mfc_status mfc_rk3_stage(mfc_ctx* ctx, int32_t stage, const double* q_in, const double* q_n, double* q_out,
+                         double dt, void* stream);
 
 /* nsteps RK3 steps in place, each with its own CFL dt (dt <= 0) or the
  * fixed dt.  dt_log (nullable) is a DEVICE array of nsteps doubles. */
@@ -284,8 +316,12 @@ mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const do
  * before any stream capture.  All calls share the one array, which keeps
  * the last call's contents: calls that overlap on the GPU (concurrent
  * streams, several host threads) race and must be serialised by the
- * caller.  Non-physical states are not reported by this call (no context
- * holds the flag).  Errors: mfc_last_error(NULL). */
+ * caller.  A non-physical state met during the step (rho <= 0 or c^2 <= 0,
+ * reported as MFC_ERR_NONPHYSICAL by the context calls) is reported here
+ * through dt_used, which then holds NaN; with dt_used = NULL it is not
+ * reported.  The cached address belongs to the device's current context: a
+ * device reset (cudaDeviceReset) invalidates it, so this call must not be
+ * used on a device after its reset.  Errors: mfc_last_error(NULL). */
 #define MFC_NOALLOC_SCRATCH_DOUBLES 8388608
 mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* opts, double* q,
                                 double dt, double* dt_used, void* stream);

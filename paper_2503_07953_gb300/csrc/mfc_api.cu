@@ -4,6 +4,7 @@
 // mfc_vjp.cuh.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -184,8 +185,9 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
             if (!(g->hi[a] > g->lo[a]) || !std::isfinite(g->hi[a] - g->lo[a])) return "need lo < hi on active axes";
             for (int s = 0; s < 2; ++s) {
                 const int bc = s ? g->bc_hi[a] : g->bc_lo[a];
-                if (bc < 0 || bc > 2) return "unknown boundary condition";
-                if (bc != MFC_BC_TRANSMISSIVE && g->n[a] < 3) return "periodic / reflective axes need n >= 3";
+                if (bc < 0 || bc > 3) return "unknown boundary condition";
+                if (bc != MFC_BC_TRANSMISSIVE && g->n[a] < 3) return "periodic / reflective / halo axes need n >= 3";
+                if (bc == MFC_BC_HALO && g->ghost < 3) return "a halo side needs ghost >= 3";
             }
             if ((g->bc_lo[a] == MFC_BC_PERIODIC) != (g->bc_hi[a] == MFC_BC_PERIODIC))
                 return "periodic must be set on both ends of an axis";
@@ -213,7 +215,14 @@ std::string check_description(const mfc_grid* g, const mfc_eos* e, const mfc_opt
     if (o->low_mach == 2 && o->riemann != 0) return "the anti-dissipation pressure correction needs HLLC";
     if (!(o->weno_eps > 0.0) || !std::isfinite(o->weno_eps)) return "weno_eps must be > 0";
     if (!(o->cfl > 0.0) || !std::isfinite(o->cfl)) return "cfl must be > 0";
+    if (o->viscous_dt != 0 && o->viscous_dt != 1) return "viscous_dt must be 0 or 1";
     return "";
+}
+
+bool has_halo(const mfc_grid* g) {
+    for (int a = 0; a < g->ndim; ++a)
+        if (g->bc_lo[a] == MFC_BC_HALO || g->bc_hi[a] == MFC_BC_HALO) return true;
+    return false;
 }
 
 void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Consts& C, int64_t& total) {
@@ -271,6 +280,10 @@ void make_consts(const mfc_grid* g, const mfc_eos* e, const mfc_opts* o, mfc::Co
         if (C.eta[i] > 0.0) C.viscous = 1;
     }
     C.cfl = o->cfl;
+    C.visc_dt = (o->viscous_dt != 0 && C.viscous) ? 1 : 0;
+    C.dx2min = C.dx[0] * C.dx[0];
+    for (int a = 1; a < g->ndim; ++a) C.dx2min = (C.dx[a] * C.dx[a] < C.dx2min) ? C.dx[a] * C.dx[a] : C.dx2min;
+    C.inv_dx2min = 1.0 / C.dx2min;
     total = C.fstride * C.nq;
 }
 
@@ -720,6 +733,12 @@ mfc_status mfc_init(const mfc_grid* grid, const mfc_eos* eos, const mfc_opts* op
         g_init_error = why;
         return MFC_ERR_ARG;
     }
+    bool viscous = false;
+    for (int i = 0; i < eos->nfluids; ++i) viscous = viscous || eos->eta[i] > 0.0;
+    if (viscous && has_halo(grid)) {
+        g_init_error = "halo sides (MFC_BC_HALO) are not supported with viscosity";
+        return MFC_ERR_UNSUPPORTED;
+    }
     mfc_ctx* ctx = new (std::nothrow) mfc_ctx();
     if (!ctx) {
         g_init_error = "host allocation failed";
@@ -824,16 +843,42 @@ mfc_status mfc_rhs(mfc_ctx* ctx, const double* q, double* rhs, void* stream) {
     return eval_L(ctx, q, rhs, 0, nullptr, nullptr, 0.0, 0.0, (cudaStream_t)stream);
 }
 
+#define MFC_REFUSE_HALO(ctx)                                                                              \
+    do {                                                                                                  \
+        if (has_halo(&(ctx)->grid))                                                                       \
+            return fail(ctx, MFC_ERR_UNSUPPORTED,                                                         \
+                        "a context with halo sides steps stage by stage (mfc_rk3_stage), the halos "      \
+                        "refreshed between stages");                                                     \
+    } while (0)
+
 mfc_status mfc_rk3_step(mfc_ctx* ctx, double* q, double dt, double* dt_used, void* stream) {
     MFC_CHECK_CTX(ctx);
+    MFC_REFUSE_HALO(ctx);
     if (!q) return fail(ctx, MFC_ERR_ARG, "null buffer");
     if (!std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "dt must be finite");
     DeviceGuard guard(ctx->device);
     return rk3_once(ctx, q, dt, dt_used, (cudaStream_t)stream);
 }
 
+mfc_status mfc_rk3_stage(mfc_ctx* ctx, int32_t stage, const double* q_in, const double* q_n, double* q_out,
+                         double dt, void* stream) {
+    MFC_CHECK_CTX(ctx);
+    if (stage < 1 || stage > 3) return fail(ctx, MFC_ERR_ARG, "stage must be 1, 2 or 3");
+    if (!q_in || !q_out || (stage > 1 && !q_n)) return fail(ctx, MFC_ERR_ARG, "null buffer");
+    if (q_out == q_in) return fail(ctx, MFC_ERR_ARG, "q_out must not alias q_in");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "a stage needs the step's dt > 0");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mfc_status st = eval_dt(ctx, q_in, dt, s);
+    if (st != MFC_OK) return st;
+    if (stage == 1) return eval_L(ctx, q_in, ctx->r, 1, nullptr, q_out, 0.0, 1.0, s);
+    if (stage == 2) return eval_L(ctx, q_in, ctx->r, 2, q_n, q_out, RK_A2, RK_B2, s);
+    return eval_L(ctx, q_in, ctx->r, 2, q_n, q_out, RK_A3, RK_B3, s);
+}
+
 mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, double* dt_log, void* stream) {
     MFC_CHECK_CTX(ctx);
+    MFC_REFUSE_HALO(ctx);
     if (!q || nsteps < 0) return fail(ctx, MFC_ERR_ARG, "null buffer or negative step count");
     if (!std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "dt must be finite");
     DeviceGuard guard(ctx->device);
@@ -847,6 +892,7 @@ mfc_status mfc_rk3_run(mfc_ctx* ctx, double* q, int32_t nsteps, double dt, doubl
 mfc_status mfc_rk3_step_batch_host(mfc_ctx* ctx, int32_t count, const double* const* q_in, double* const* q_out,
                                    double dt, double* dt_used, void* stream) {
     MFC_CHECK_CTX(ctx);
+    MFC_REFUSE_HALO(ctx);
     if (count < 0) return fail(ctx, MFC_ERR_ARG, "negative state count");
     if (count == 0) return MFC_OK;
     if (!q_in || !q_out) return fail(ctx, MFC_ERR_ARG, "null pointer array");
@@ -876,6 +922,7 @@ mfc_status mfc_rk3_step_batch_host(mfc_ctx* ctx, int32_t count, const double* co
 
 mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, double* q_bar, void* stream) {
     MFC_CHECK_CTX(ctx);
+    MFC_REFUSE_HALO(ctx);
     if (!q || !rhs_bar || !q_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
     if (q_bar == q || q_bar == rhs_bar) return fail(ctx, MFC_ERR_ARG, "q_bar must not alias q or rhs_bar");
     if (ctx->C.viscous) return fail(ctx, MFC_ERR_UNSUPPORTED, "the adjoint of the viscous term is not implemented");
@@ -886,6 +933,7 @@ mfc_status mfc_rhs_vjp(mfc_ctx* ctx, const double* q, const double* rhs_bar, dou
 mfc_status mfc_rk3_step_vjp(mfc_ctx* ctx, const double* q_n, double dt, const double* qnp1_bar, double* qn_bar,
                             void* stream) {
     MFC_CHECK_CTX(ctx);
+    MFC_REFUSE_HALO(ctx);
     if (!q_n || !qnp1_bar || !qn_bar) return fail(ctx, MFC_ERR_ARG, "null buffer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, MFC_ERR_ARG, "the adjoint needs the step's dt > 0");
     if (qn_bar == q_n || qnp1_bar == q_n) return fail(ctx, MFC_ERR_ARG, "bars must not alias q_n");
@@ -939,7 +987,16 @@ constexpr int64_t kNoallocScalarDoubles = 32;  // 256 bytes in front of the stat
 static __device__ __align__(256) double g_noalloc_scratch[MFC_NOALLOC_SCRATCH_DOUBLES];
 
 constexpr int kNoallocMaxDevices = 64;
-double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+// Device address of the array on each device, looked up by the first call on
+// that device.  Concurrent first calls may both look it up; they store the
+// same value.
+std::atomic<double*> g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// dt_used = NaN when the step met a non-physical state (the flag the step's
+// kernels set), so that a caller without a context can still see it.
+__global__ void flag_to_dt_kernel(const DevScalars* s, double* dt_out) {
+    if (s->flag) *dt_out = __longlong_as_double(0x7ff8000000000000LL);
+}
 
 }  // namespace
 
@@ -953,6 +1010,10 @@ extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* 
     if (!q || !std::isfinite(dt)) {
         g_init_error = "null state or non-finite dt";
         return MFC_ERR_ARG;
+    }
+    if (has_halo(grid)) {
+        g_init_error = "the allocation-free step has no halo exchange between its stages";
+        return MFC_ERR_UNSUPPORTED;
     }
     mfc_ctx ctx;
     make_consts(grid, eos, opts, ctx.C, ctx.total);
@@ -972,16 +1033,17 @@ extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* 
         return MFC_ERR_CUDA;
     }
     // once per device, with that device current: the device address of the array
-    if (!g_noalloc_ptr[dev]) {
+    double* base = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!base) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             g_init_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return MFC_ERR_CUDA;
         }
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+        base = static_cast<double*>(p);
+        g_noalloc_ptr[dev].store(base, std::memory_order_release);
     }
-    double* base = g_noalloc_ptr[dev];
     ctx.grid = *grid;
     ctx.eos = *eos;
     ctx.opts = *opts;
@@ -1000,6 +1062,16 @@ extern "C" mfc_status mfc_rk3_step_noalloc(const mfc_grid* grid, const mfc_eos* 
         return MFC_ERR_CUDA;
     }
     const mfc_status st = rk3_once(&ctx, q, dt, dt_used, s);
-    if (st != MFC_OK) g_init_error = ctx.err;
-    return st;
+    if (st != MFC_OK) {
+        g_init_error = ctx.err;
+        return st;
+    }
+    if (dt_used) {
+        flag_to_dt_kernel<<<1, 1, 0, s>>>(ctx.scal, dt_used);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            g_init_error = std::string("flag kernel: ") + cudaGetErrorString(e);
+            return MFC_ERR_CUDA;
+        }
+    }
+    return MFC_OK;
 }

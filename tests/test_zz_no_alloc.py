@@ -45,9 +45,15 @@ def descriptors(mfc, case, ghost=3, precision=0):
     return g, e, o
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_noalloc_step_matches_context_step(mfc_lib, cuda_device, precision):
-    """Two calls in a row (CFL dt each) agree with mfc_rk3_step on a context."""
+    """Two calls in a row (CFL dt each) agree with mfc_rk3_step on a context
+    in every precision.  MFC_FP64, MFC_MIXED and MFC_FP64_FAST run the same
+    kernels either way and agree bit for bit, dt included.  A double-float
+    context runs its sweeps split into reconstruction and Riemann kernels
+    and this call the fused sweep; the compiler contracts their updates
+    differently, so they agree to rounding: the first dt (from the common
+    initial state) bit for bit, the second to 1e-12."""
     case, W = wl.shock_bubble_3d(dims=(40, 36, 30))
     S = solver_for(mfc_lib, case, precision=precision)
     q_ctx = S.prim_to_cons(S.from_interior(W))
@@ -63,8 +69,34 @@ def test_noalloc_step_matches_context_step(mfc_lib, cuda_device, precision):
         a, b = to_host(S, q_na), to_host(S, q_ctx)
         err = case_errors(case, a, b)
         assert (err <= TOL).all(), (call, err)
-        assert dts[2 * call].item() == dts[2 * call + 1].item()
+        d_ctx, d_na = dts[2 * call].item(), dts[2 * call + 1].item()
+        if precision != mfc_lib.MFC_DF64 or call == 0:
+            assert d_ctx == d_na
+        else:
+            assert abs(d_na - d_ctx) <= 1e-12 * d_ctx
     S.check()
+
+
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+def test_noalloc_reports_nonphysical_state_in_dt(mfc_lib, cuda_device, dt):
+    """Without a context there is no flag to read back: a step that meets a
+    non-physical state (here a cell of negative pressure) returns NaN in
+    dt_used; the next call on a good state clears it."""
+    case, W = wl.shock_bubble_3d(dims=(20, 18, 16))
+    S = solver_for(mfc_lib, case)
+    q_good = S.prim_to_cons(S.from_interior(W))
+    Wbad = W.copy()
+    Wbad[case.nf + case.ndim, 7, 9, 10] = -0.5  # p < 0 with pi_inf = 0: c^2 < 0
+    q_bad = S.prim_to_cons(S.from_interior(Wbad))
+    g, e, o = descriptors(mfc_lib, case)
+    stream = torch.cuda.current_stream().cuda_stream
+    dt_used = torch.zeros(1, dtype=torch.float64, device=cuda_device)
+    mfc_lib.mfc_rk3_step_noalloc(g, e, o, q_bad.data_ptr(), dt, dt_used.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert np.isnan(dt_used.item())
+    mfc_lib.mfc_rk3_step_noalloc(g, e, o, q_good.data_ptr(), dt, dt_used.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert np.isfinite(dt_used.item()) and dt_used.item() > 0
 
 
 def test_noalloc_rejects_oversize_grid(mfc_lib, cuda_device):
