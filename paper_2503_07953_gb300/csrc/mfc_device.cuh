@@ -44,7 +44,7 @@ struct Consts {
     int64_t stride[3];        // element stride of one cell step along x, y, z
     int64_t fstride;          // elements per field
     int64_t origin;           // element offset of interior cell (0, 0, 0)
-    int bc_lo[3], bc_hi[3];   // 0 periodic, 1 transmissive, 2 reflective
+    int bc_lo[3], bc_hi[3];   // 0 periodic, 1 transmissive, 2 reflective, 3 halo
     double dx[3], inv_dx[3];
     double g[MAXF], h[MAXF];  // 1/(gamma_i - 1), gamma_i pi_i/(gamma_i - 1)
     float gf[MAXF], hf[MAXF];
@@ -64,9 +64,12 @@ struct Consts {
     double eta[MAXF];         // phasic shear viscosities
     float etaf[MAXF];
     double cfl;
+    int visc_dt;              // 1: the CFL dt also takes the explicit viscous limit
+    double dx2min;            // min over active axes of dx_d^2
+    double inv_dx2min;        // 1 / dx2min
 };
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_HALO = 3 };
 enum { WENO_JS = 0, WENO_M = 1, WENO_Z = 2, WENO_TENO = 3 };
 
 template <int NF, int ND>
@@ -493,17 +496,15 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
     const df64 Q[3] = {D01 - df_scale(D12, 4.0f), -(df_scale(D12, 2.0f) + D23),
                        df_scale(D34, 2.0f) - df_mulf(D23, 5.0f)};
     const double dR[3] = {0.1, 0.6, 0.3}, dL[3] = {0.3, 0.6, 0.1};
-    df64 omR[3], omL[3];
+    // the weights of the (right, left) edges, stencil by stencil
+    df64x2 om[3];
     const float th = fmaxf(fmaxf(t[0].hi, t[1].hi), t[2].hi);
     WenoEdges out;
     // an indicator that overflowed is inf or NaN, and so is the sum
     out.bad = !((t[0].hi + t[1].hi) + t[2].hi <= 0x1.fffffep127f);
     if (!(th >= 0x1p-120f)) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            omR[r] = df64(dR[r]);
-            omL[r] = df64(dL[r]);
-        }
+        for (int r = 0; r < 3; ++r) om[r] = dfx2(dR[r], dL[r]);
     } else {
         int k = ((__float_as_int(th) >> 23) & 0xff) - 127;
         k = k > 126 ? 126 : k;
@@ -526,16 +527,12 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
 #pragma unroll
             for (int r = 0; r < 3; ++r) B[r] = B[r] * iAm;
             if (variant == WENO_Z) {
+                df64x2 x[3];
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const double* d = side ? dL : dR;
-                    df64* om = side ? omL : omR;
-                    const df64 x0 = df64(d[0]) * B[0], x1 = df64(d[1]) * B[1], x2 = df64(d[2]) * B[2];
-                    const df64 inv = df_div(one, (x0 + x1) + x2);
-                    om[0] = x0 * inv;
-                    om[1] = x1 * inv;
-                    om[2] = x2 * inv;
-                }
+                for (int r = 0; r < 3; ++r) x[r] = dfx2(dR[r], dL[r]) * dfx2(B[r], B[r]);
+                const df64x2 inv = df_rcp((x[0] + x[1]) + x[2]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) om[r] = x[r] * inv;
             } else {
                 // TENO: gamma_r = d_r B_r^6; stencil r off when gamma_r < C_T sum
                 // gamma, the others at d_r renormalised
@@ -545,20 +542,23 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
                     const df64 x2 = B[r] * B[r];
                     x6[r] = x2 * (x2 * x2);
                 }
+                df64 omR[3], omL[3];
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     const double* d = side ? dL : dR;
-                    df64* om = side ? omL : omR;
+                    df64* os = side ? omL : omR;
                     const df64 y0 = df64(d[0]) * x6[0], y1 = df64(d[1]) * x6[1], y2 = df64(d[2]) * x6[2];
                     const df64 lim = cT * ((y0 + y1) + y2);
                     const df64 b0 = (y0 < lim) ? df64(0.0) : df64(d[0]);
                     const df64 b1 = (y1 < lim) ? df64(0.0) : df64(d[1]);
                     const df64 b2 = (y2 < lim) ? df64(0.0) : df64(d[2]);
                     const df64 inv = df_div(one, (b0 + b1) + b2);
-                    om[0] = b0 * inv;
-                    om[1] = b1 * inv;
-                    om[2] = b2 * inv;
+                    os[0] = b0 * inv;
+                    os[1] = b1 * inv;
+                    os[2] = b2 * inv;
                 }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) om[r] = dfx2(omR[r], omL[r]);
             }
         } else {
             // JS and mapped: alpha_r proportional to d_r (t_min / t_r)^2
@@ -570,37 +570,35 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
                 const df64 u = df_div(tmin, ts[r]);
                 u2[r] = u * u;
             }
+            // both edges at once, the right edge in lane x, the left in lane y
+            df64x2 w[3];
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const double* d = side ? dL : dR;
-                df64* om = side ? omL : omR;
-                df64 w[3];
+            for (int r = 0; r < 3; ++r) w[r] = dfx2(dR[r], dL[r]) * dfx2(u2[r], u2[r]);
+            df64x2 inv = df_rcp((w[0] + w[1]) + w[2]);
 #pragma unroll
-                for (int r = 0; r < 3; ++r) w[r] = df64(d[r]) * u2[r];
-                df64 inv = df_div(one, (w[0] + w[1]) + w[2]);
+            for (int r = 0; r < 3; ++r) w[r] = w[r] * inv;
+            if (variant == WENO_M) {
+                // g_r(w) = w (d + d^2 - 3 d w + w^2) / (d^2 + w (1 - 2 d)), renormalised
+                df64x2 N[3], D[3];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) w[r] = w[r] * inv;
-                if (variant == WENO_M) {
-                    // g_r(w) = w (d + d^2 - 3 d w + w^2) / (d^2 + w (1 - 2 d)), renormalised
-                    df64 N[3], D[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        N[r] = w[r] * (df64(d[r] * (1.0 + d[r])) + w[r] * (w[r] - df64(3.0 * d[r])));
-                        D[r] = df64(d[r] * d[r]) + w[r] * df64(1.0 - 2.0 * d[r]);
-                    }
-                    const df64 gm0 = N[0] * (D[1] * D[2]), gm1 = N[1] * (D[0] * D[2]), gm2 = N[2] * (D[0] * D[1]);
-                    inv = df_div(one, (gm0 + gm1) + gm2);
-                    w[0] = gm0 * inv;
-                    w[1] = gm1 * inv;
-                    w[2] = gm2 * inv;
+                for (int r = 0; r < 3; ++r) {
+                    N[r] = w[r] * (dfx2(dR[r] * (1.0 + dR[r]), dL[r] * (1.0 + dL[r])) +
+                                   w[r] * (w[r] - dfx2(3.0 * dR[r], 3.0 * dL[r])));
+                    D[r] = dfx2(dR[r] * dR[r], dL[r] * dL[r]) + w[r] * dfx2(1.0 - 2.0 * dR[r], 1.0 - 2.0 * dL[r]);
                 }
-#pragma unroll
-                for (int r = 0; r < 3; ++r) om[r] = w[r];
+                const df64x2 gm0 = N[0] * (D[1] * D[2]), gm1 = N[1] * (D[0] * D[2]), gm2 = N[2] * (D[0] * D[1]);
+                inv = df_rcp((gm0 + gm1) + gm2);
+                w[0] = gm0 * inv;
+                w[1] = gm1 * inv;
+                w[2] = gm2 * inv;
             }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) om[r] = w[r];
         }
     }
-    const df64 cr = ((omR[0] * P[0] + omR[1] * P[1]) + omR[2] * P[2]) * sixth;
-    const df64 cl = ((omL[0] * Q[0] + omL[1] * Q[1]) + omL[2] * Q[2]) * sixth;
+    const df64x2 c = ((om[0] * dfx2(P[0], Q[0]) + om[1] * dfx2(P[1], Q[1])) + om[2] * dfx2(P[2], Q[2])) *
+                     dfx2(sixth, sixth);
+    const df64 cr = lane_x(c), cl = lane_y(c);
     out.vr = f2 + (f64_from_f32_bits(cr.hi) + f64_from_f32_bits(cr.lo));
     out.vl = f2 + (f64_from_f32_bits(cl.hi) + f64_from_f32_bits(cl.lo));
     return out;
@@ -690,11 +688,87 @@ __device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f
     vl = fma(iL, sL, f2);
 }
 
+// MODE_MIXED WENO5 of one cell (JS, mapped and Z weights) in float32: the
+// formulation of weno5_cell_fast64 on consecutive differences, with the
+// indicators divided by their sum and eps floored at 1e-9 of it (as
+// weno5_scaled_beta does, so that every product of the weights stays inside
+// the float32 range), and the right- and left-edge weights carried as the two
+// lanes of float2 values: each paired add, multiply or fused multiply-add is
+// one instruction for both edges (FADD2 / FMUL2 / FFMA2).
+__device__ __forceinline__ float2 pair(float r, float l) { return make_float2(r, l); }
+
+__device__ __forceinline__ void weno5_cell_mixed32(float f0, float f1, float f2, float f3, float f4, int variant,
+                                                   float eps, float& vl, float& vr) {
+    const float D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
+    const float a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const float g[3] = {fmaf(3.0f, D12, -D01), D12 + D23, fmaf(-3.0f, D23, D34)};
+    float b[3];  // 4 beta_r
+#pragma unroll
+    for (int r = 0; r < 3; ++r) b[r] = fmaf((13.0f / 3.0f) * a[r], a[r], g[r] * g[r]);
+    const float scale = __fdividef(1.0f, (b[0] + b[1]) + (b[2] + 4e-30f));
+    const float e = fmaxf(4.0f * eps * scale, 1e-9f);
+    float t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = fmaf(b[r], scale, e);
+    float P[3];
+    if (variant == WENO_Z) {
+        const float tau = fabsf(t[0] - t[2]);
+        P[0] = (t[0] + tau) * (t[1] * t[2]);
+        P[1] = (t[1] + tau) * (t[0] * t[2]);
+        P[2] = (t[2] + tau) * (t[0] * t[1]);
+    } else {
+        const float s0 = t[0] * t[0], s1 = t[1] * t[1], s2 = t[2] * t[2];
+        P[0] = s1 * s2;
+        P[1] = s0 * s2;
+        P[2] = s0 * s1;
+    }
+    // (right, left) unnormalised weights: alpha_r = d_r P_r
+    const float2 d0 = pair(0.1f, 0.3f), d1 = pair(0.6f, 0.6f), d2 = pair(0.3f, 0.1f);
+    float2 w0 = __fmul2_rn(d0, pair(P[0], P[0]));
+    float2 w1 = __fmul2_rn(d1, pair(P[1], P[1]));
+    float2 w2 = __fmul2_rn(d2, pair(P[2], P[2]));
+    float2 nrm = __fadd2_rn(__fadd2_rn(w0, w1), w2);
+    float2 inv;
+    if (variant == WENO_M) {
+        // Henrick's map of the normalised JS weights x: numerator
+        // x (d + d^2 + x (x - 3 d)) times the other stencils' denominators
+        // d^2 + x (1 - 2 d)
+        inv = pair(__fdividef(1.0f, nrm.x), __fdividef(1.0f, nrm.y));
+        const float2 x0 = __fmul2_rn(w0, inv), x1 = __fmul2_rn(w1, inv), x2 = __fmul2_rn(w2, inv);
+        const float2 N0 = __fmul2_rn(x0, __ffma2_rn(x0, __fadd2_rn(x0, pair(-0.3f, -0.9f)), pair(0.11f, 0.39f)));
+        const float2 N1 = __fmul2_rn(x1, __ffma2_rn(x1, __fadd2_rn(x1, pair(-1.8f, -1.8f)), pair(0.96f, 0.96f)));
+        const float2 N2 = __fmul2_rn(x2, __ffma2_rn(x2, __fadd2_rn(x2, pair(-0.9f, -0.3f)), pair(0.39f, 0.11f)));
+        const float2 E0 = __ffma2_rn(x0, pair(0.8f, 0.4f), pair(0.01f, 0.09f));
+        const float2 E1 = __ffma2_rn(x1, pair(-0.2f, -0.2f), pair(0.36f, 0.36f));
+        const float2 E2 = __ffma2_rn(x2, pair(0.4f, 0.8f), pair(0.09f, 0.01f));
+        w0 = __fmul2_rn(N0, __fmul2_rn(E1, E2));
+        w1 = __fmul2_rn(N1, __fmul2_rn(E0, E2));
+        w2 = __fmul2_rn(N2, __fmul2_rn(E0, E1));
+        nrm = __fadd2_rn(__fadd2_rn(w0, w1), w2);
+    }
+    // 1 / (12 n) per edge
+    inv = pair(__fdividef(1.0f, 12.0f * nrm.x), __fdividef(1.0f, 12.0f * nrm.y));
+    // 12 (candidate_r - f2) of the (right, left) edges: a_r +- 3 s_r g_r
+    const float2 c0 = __ffma2_rn(pair(3.0f, -3.0f), pair(g[0], g[0]), pair(a[0], a[0]));
+    const float2 c1 = __ffma2_rn(pair(3.0f, -3.0f), pair(g[1], g[1]), pair(a[1], a[1]));
+    const float2 c2 = __ffma2_rn(pair(-3.0f, 3.0f), pair(g[2], g[2]), pair(a[2], a[2]));
+    const float2 sum = __ffma2_rn(w2, c2, __ffma2_rn(w1, c1, __fmul2_rn(w0, c0)));
+    const float2 v = __ffma2_rn(inv, sum, pair(f2, f2));
+    vr = v.x;
+    vl = v.y;
+}
+
 template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int variant, R eps, R ct, R& vl, R& vr) {
     if constexpr (MODE == MODE_FAST) {
         if (variant != WENO_TENO) {
             weno5_cell_fast64(f0, f1, f2, f3, f4, variant, eps, vl, vr);
+            return;
+        }
+    }
+    if constexpr (MODE == MODE_MIXED) {
+        if (variant != WENO_TENO) {
+            weno5_cell_mixed32(f0, f1, f2, f3, f4, variant, eps, vl, vr);
             return;
         }
     }
@@ -962,15 +1036,19 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
 
 // Index of the interior cell that supplies the value of cell c along an
 // axis with n cells (Sec. 3.3): periodic wrap, transmissive copy of the
-// nearest cell, reflective mirror (flip = normal momentum changes sign).
+// nearest cell, reflective mirror (flip = normal momentum changes sign); a
+// halo side supplies the ghost cell itself (the caller's copy of the
+// neighbouring subdomain's cell).
 __device__ __forceinline__ int64_t bc_source(int64_t c, int64_t n, int bclo, int bchi, bool& flip) {
     if (c < 0) {
+        if (bclo == BC_HALO) return c;
         if (bclo == BC_PERIODIC) return c + n;
         if (bclo == BC_TRANSMISSIVE) return 0;
         flip = true;
         return -1 - c;
     }
     if (c >= n) {
+        if (bchi == BC_HALO) return c;
         if (bchi == BC_PERIODIC) return c - n;
         if (bchi == BC_TRANSMISSIVE) return n - 1;
         flip = true;

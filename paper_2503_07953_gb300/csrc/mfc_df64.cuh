@@ -149,6 +149,65 @@ __device__ __forceinline__ double f64_from_f32_bits(float x) {
     return __hiloint2double((int)((b & 0x80000000u) | (de << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// Two double-float numbers side by side, in the x and y lanes of float2
+// leading and trailing parts.  Every step of the operations below is one
+// paired float32 instruction for both numbers (FADD2, FMUL2, FFMA2 on
+// sm_100 and later), with the same rounding as the scalar operations above
+// lane by lane: for two computations that perform the same operations on
+// different values, such as the right- and left-edge weights of WENO5.
+struct df64x2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ df64x2 dfx2(df64 x, df64 y) {
+    return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)};
+}
+__device__ __forceinline__ df64x2 dfx2(double x, double y) { return dfx2(df64(x), df64(y)); }
+__device__ __forceinline__ df64 lane_x(df64x2 a) { return df64(a.hi.x, a.lo.x); }
+__device__ __forceinline__ df64 lane_y(df64x2 a) { return df64(a.hi.y, a.lo.y); }
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+__device__ __forceinline__ df64x2 df_fast2sum(float2 s, float2 e) {
+    const float2 h = __fadd2_rn(s, e);
+    return {h, sub2(e, sub2(h, s))};
+}
+
+__device__ __forceinline__ df64x2 operator+(df64x2 a, df64x2 b) {
+    const float2 s = __fadd2_rn(a.hi, b.hi);
+    const float2 v = sub2(s, a.hi);
+    float2 e = __fadd2_rn(sub2(a.hi, sub2(s, v)), sub2(b.hi, v));
+    e = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
+    return df_fast2sum(s, e);
+}
+
+__device__ __forceinline__ df64x2 operator-(df64x2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ df64x2 operator-(df64x2 a, df64x2 b) { return a + (-b); }
+
+__device__ __forceinline__ df64x2 operator*(df64x2 a, df64x2 b) {
+    const float2 p = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    return df_fast2sum(p, e);
+}
+
+// 1 / b lane by lane, as df_div(1, b)
+__device__ __forceinline__ df64x2 df_rcp(df64x2 b) {
+    float2 r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r.x) : "f"(b.hi.x));
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r.y) : "f"(b.hi.y));
+    r = __ffma2_rn(r, __ffma2_rn(neg2(b.hi), r, make_float2(1.0f, 1.0f)), r);
+    const float2 q1 = r;
+    const float2 p = __fmul2_rn(q1, b.hi);
+    const float2 pe = __ffma2_rn(q1, b.hi, neg2(p));
+    float2 rem = sub2(make_float2(1.0f, 1.0f), p);
+    rem = sub2(rem, pe);
+    rem = __ffma2_rn(neg2(q1), b.lo, rem);
+    return df_fast2sum(q1, __fmul2_rn(rem, r));
+}
+
 // Comparisons of normalised pairs: by the leading part, then the trailing part.
 __device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }

@@ -183,6 +183,203 @@ __global__ void __launch_bounds__(128, 4) sweep_kernel_mixed(const Consts C, con
     sweep_body<NF, ND, DIR, MODE_MIXED>(C, A);
 }
 
+// Asynchronous global -> shared copies of 4 or 8 bytes (cp.async), their
+// commit groups and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory rings of the staged mixed sweep, per thread: kStageQ slots
+// of the conservative state of one cell, kStageU slots of the accumulator
+// (float) and q^n of one cell, each value at [slot][field][thread].
+constexpr int kStageQ = 5;
+constexpr int kStageU = 2;
+template <int NQ>
+constexpr int staged_smem_bytes(int block) {
+    return block * (kStageQ * NQ * 8 + kStageU * NQ * (8 + 4));
+}
+
+// The y and z sweeps of the mixed mode with their global loads staged
+// through shared memory.  Each thread marches its line segment exactly as
+// sweep_body<MODE_MIXED> does (same arithmetic in the same order, so the
+// results are identical); its loads are asynchronous copies into per-thread
+// rings, issued one cell ahead of their use: group g holds the state of cell
+// s0 - 3 + g (the window's new cell when g >= 4) and the accumulator and
+// q^n of cell s0 - 6 + g (the cell finished while group g is consumed).  The
+// copies of a warp are contiguous along x, and the march waits only for
+// copies issued an iteration earlier, so the latency of the loads (L2 or
+// HBM) overlaps the reconstruction and Riemann solve of the previous cell
+// instead of stalling the update.  The state of the finished cell, needed
+// by the stage update, is still in the state ring (group g - 3).
+template <int NF, int ND, int DIR>
+__device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepArgs& A) {
+    using L = Lay<NF, ND>;
+    using R = float;
+    constexpr int NQ = L::NQ;
+    constexpr int TA = 0;
+    constexpr int TB = (DIR == 2) ? 1 : 2;
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    const int bd = blockDim.x, tx = threadIdx.x;
+    double* ringQ = reinterpret_cast<double*>(stage_raw);
+    double* ringN = ringQ + kStageQ * NQ * bd;
+    float* ringF = reinterpret_cast<float*>(ringN + kStageU * NQ * bd);
+    auto Q = [&](int slot, int f) -> double* { return ringQ + (slot * NQ + f) * bd + tx; };
+    auto QN = [&](int slot, int f) -> double* { return ringN + (slot * NQ + f) * bd + tx; };
+    auto RF = [&](int slot, int f) -> float* { return ringF + (slot * NQ + f) * bd + tx; };
+
+    const int64_t nta = C.n[TA], ntb = C.n[TB];
+    const int64_t nlines = nta * ntb;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nlines * A.nseg) return;
+    const int64_t line = tid % nlines;
+    const int64_t seg = tid / nlines;
+    const int64_t ia = line % nta, ib = line / nta;
+    const int64_t base = C.origin + ia * C.stride[TA] + ib * C.stride[TB];
+    const int64_t S = C.stride[DIR];
+    const int64_t n = C.n[DIR];
+    const int64_t s0 = seg * A.seg;
+    const int64_t s1 = (s0 + A.seg < n) ? s0 + A.seg : n;
+    const int bclo = C.bc_lo[DIR], bchi = C.bc_hi[DIR];
+    const int variant = C.weno;
+    const R eps = C.epsf, ct = C.teno_ctf, inv_dx = C.inv_dxf[DIR];
+    const bool acc = A.acc_in == 2, upd2 = A.out_kind == 2;
+    bool bad = false;
+
+    const int64_t G = (s1 - s0) + 6;
+    int64_t issued = 0;
+    auto issue = [&]() {
+        if (issued < G) {
+            const int slot = (int)(issued % kStageQ);
+            bool flip = false;
+            const int64_t cc = bc_source(s0 - 3 + issued, n, bclo, bchi, flip);
+            const double* p = A.q + base + cc * S;
+#pragma unroll
+            for (int f = 0; f < NQ; ++f) cp_async8(Q(slot, f), p + f * C.fstride);
+            const int64_t u = s0 - 6 + issued;
+            if (u >= s0 && u < s1) {
+                const int us = (int)(issued % kStageU);
+                const int64_t o = base + u * S;
+                if (acc) {
+#pragma unroll
+                    for (int f = 0; f < NQ; ++f) cp_async4(RF(us, f), A.rhsf + o + f * C.fstride);
+                }
+                if (upd2) {
+#pragma unroll
+                    for (int f = 0; f < NQ; ++f) cp_async8(QN(us, f), A.qn + o + f * C.fstride);
+                }
+            }
+        }
+        cp_async_commit();
+        ++issued;
+    };
+    // primitive state of the cell of group g, from its ring slot
+    auto prim_of = [&](int64_t g, R* out) {
+        bool flip = false;
+        bc_source(s0 - 3 + g, n, bclo, bchi, flip);
+        const int slot = (int)(g % kStageQ);
+        double qc[NQ];
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) qc[f] = *Q(slot, f);
+        if (flip) qc[L::MOM + DIR] = -qc[L::MOM + DIR];
+        prim_for_recon<NF, ND, MODE_MIXED, R>(qc, out, C, bad);
+    };
+
+    issue();  // group 0; one group is always in flight ahead of the one in use
+    R W[5][NQ];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        issue();
+        cp_async_wait<1>();
+        prim_of(k, W[k]);
+    }
+
+    R WLprev[NQ], Fprev[NQ], uprev = R(0);
+    const double dtv = (A.out_kind != 0) ? *A.dt : 0.0;
+
+    for (int64_t m = s0 - 1; m <= s1; ++m) {
+        const int64_t g = m + 5 - s0;
+        issue();
+        cp_async_wait<1>();
+        prim_of(g, W[4]);
+        R WRm[NQ], WLm[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k)
+            weno5_cell<MODE_MIXED, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
+        if (m >= s0) {
+            if (!physical_state<NF, ND, R, MODE_MIXED>(WLprev, C) || !physical_state<NF, ND, R, MODE_MIXED>(WRm, C)) {
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    WLprev[k] = W[1][k];
+                    WRm[k] = W[2][k];
+                }
+            }
+            R F[NQ], uf;
+            hllc<NF, ND, DIR, MODE_MIXED>(WLprev, WRm, C, F, uf, bad);
+            if (m >= s0 + 1) {
+                // finish cell m - 1 (window slot 1); its accumulator and q^n are
+                // in update slot g, its state in state slot g - 3
+                const int64_t off = base + (m - 1) * S;
+                const int us = (int)(g % kStageU), qs = (int)((g - 3) % kStageQ);
+                const R du = uf - uprev;
+                R Kc = R(0);
+                if constexpr (NF == 2) {
+                    if (C.model == 1) Kc = kapila_K<MODE_MIXED, R>(W[1][L::E], W[1][L::A], C);
+                }
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    R t = (Fprev[k] - F[k]) * inv_dx;
+                    const R ac = (k >= L::A && C.model == 1) ? W[1][k] + Kc : W[1][k];
+                    if (k >= L::A) t = t + ac * du * inv_dx;
+                    const int64_t o = off + k * C.fstride;
+                    const float Lf = acc ? *RF(us, k) + t : t;
+                    if (A.out_kind == 3) {
+                        A.rhsf[o] = Lf;
+                        continue;
+                    }
+                    const double Lc = double(Lf);
+                    const double qc = *Q(qs, k);
+                    if (A.out_kind == 0) {
+                        A.rhs[o] = Lc;
+                    } else if (A.out_kind == 1) {
+                        A.qout[o] = qc + dtv * Lc;
+                    } else {
+                        A.qout[o] = A.rk_a * *QN(us, k) + A.rk_b * (qc + dtv * Lc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) Fprev[k] = F[k];
+            uprev = uf;
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) WLprev[k] = WLm[k];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) W[s][k] = W[s + 1][k];
+    }
+    cp_async_wait<0>();
+    if (bad) atomicOr(A.flag, 1);
+}
+
+// Seven 64-thread blocks per SM (14 warps): the registers this allows and
+// seven blocks' rings fit one SM; fewer warps left the march's dependency
+// stalls exposed (8 warps: issue active 36-39 %).
+template <int NF, int ND, int DIR>
+__global__ void __launch_bounds__(64, 7) sweep_kernel_staged(const Consts C, const SweepArgs A) {
+    sweep_body_staged<NF, ND, DIR>(C, A);
+}
+
 // Value of neighbour lane + off (|off| <= 2) in the sequence formed by the
 // previous, current and next 32-cell chunks held by the warp (p, c, nx).
 template <class R>
@@ -398,6 +595,20 @@ __global__ void __launch_bounds__(256) cfl_kernel(const Consts C, const double* 
             const double s = C.dx[d] / (fabs(w[L::MOM + d]) + cs);
             m = (s < m) ? s : m;
         }
+        if (C.visc_dt) {
+            // explicit viscous limit rho min_d dx_d^2 / (2 ndim eta), eta the
+            // mixture viscosity (1 - sum alpha_j) eta_N + sum alpha_j eta_j
+            double sa = 0.0;
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) sa = sa + qc[L::A + j];
+            double eta = (1.0 - sa) * C.eta[NF - 1];
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) eta = eta + qc[L::A + j] * C.eta[j];
+            if (eta > 0.0) {
+                const double s = rho * C.dx2min / ((2.0 * ND) * eta);
+                m = (s < m) ? s : m;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -462,6 +673,13 @@ __global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const dou
         double smax = 0.0;
 #pragma unroll
         for (int d = 0; d < ND; ++d) smax = fmax(smax, (fabs(u[d]) + cs) * C.inv_dx[d]);
+        if (C.visc_dt) {
+            // the viscous limit's reciprocal, 2 ndim eta / (rho min_d dx_d^2)
+            double eta = C.eta[NF - 1];
+#pragma unroll
+            for (int j = 0; j < NF - 1; ++j) eta = fma(qc[L::A + j], C.eta[j] - C.eta[NF - 1], eta);
+            smax = fmax(smax, (2.0 * ND) * eta * irho * C.inv_dx2min);
+        }
         const double s = rcp_nr(smax);
         m = (s < m) ? s : m;
     }

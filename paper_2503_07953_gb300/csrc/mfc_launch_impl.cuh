@@ -39,6 +39,21 @@ void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream
         sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
 }
 
+// y and z sweeps of the mixed mode with shared-memory staging
+// (sweep_kernel_staged): 64-thread blocks, the rings in dynamic shared
+// memory (under 48 KB for every N_f).
+constexpr int kStagedBlock = 64;
+template <int NF, int ND, int DIR>
+void launch_sweep_staged(int64_t threads, const Consts& C, const SweepArgs& A, cudaStream_t s) {
+    constexpr int smem = staged_smem_bytes<Lay<NF, ND>::NQ>(kStagedBlock);
+    static_assert(smem <= 48 * 1024, "staged sweep rings must fit the default shared-memory limit");
+    // the largest shared-memory carveout, so that seven blocks' rings fit an SM
+    static const cudaError_t carve = cudaFuncSetAttribute(
+        sweep_kernel_staged<NF, ND, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    (void)carve;
+    sweep_kernel_staged<NF, ND, DIR><<<grid_for(threads, kStagedBlock), kStagedBlock, smem, s>>>(C, A);
+}
+
 // x sweep, one warp per line segment (sweep_x_kernel): segments of at
 // least 64 cells (32 when there are few lines), enough of them for ~32 warps
 // per SM.
@@ -91,7 +106,7 @@ cudaError_t sweep_nd(const Consts& C, int dir, int mode, SweepArgs A, cudaStream
                 if constexpr (D == 0)
                     launch_sweep_x<NF, ND, MODE_MIXED>(C, A, s);
                 else
-                    launch_sweep<NF, ND, D, MODE_MIXED>(grid, C, A, s);
+                    launch_sweep_staged<NF, ND, D>(threads, C, A, s);
             } else {
                 if constexpr (D == 0) {
                     if (few) {

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmfcgb.so")
 
 MFC_OK, MFC_ERR_ARG, MFC_ERR_ALLOC, MFC_ERR_CUDA, MFC_ERR_NONPHYSICAL, MFC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE = 0, 1, 2
+MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE, MFC_BC_HALO = 0, 1, 2, 3
 MFC_FP64, MFC_MIXED, MFC_FP64_FAST, MFC_DF64 = 0, 1, 2, 3
 MFC_WENO_JS, MFC_WENO_M, MFC_WENO_Z, MFC_WENO_TENO = 0, 1, 2, 3
 MFC_MODEL_K0, MFC_MODEL_KAPILA = 0, 1
@@ -55,7 +55,7 @@ class mfc_eos(ctypes.Structure):
 class mfc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("weno", ctypes.c_int32), ("weno_eps", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("teno_ct", ctypes.c_double), ("model", ctypes.c_int32),
-                ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32)]
+                ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32), ("viscous_dt", ctypes.c_int32)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ _SIGS = {
     "mfc_compute_dt": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     "mfc_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mfc_rk3_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _VP]),
+    "mfc_rk3_stage": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "mfc_rk3_run": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_double, _VP, _VP]),
     "mfc_rk3_step_batch_host": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                                ctypes.c_double, _VP, _VP]),
@@ -151,6 +152,10 @@ def mfc_rk3_step(ctx, q, dt, dt_used, stream) -> None:
     _err(ctx, lib().mfc_rk3_step(ctx, q, float(dt), dt_used, stream))
 
 
+def mfc_rk3_stage(ctx, stage, q_in, q_n, q_out, dt, stream) -> None:
+    _err(ctx, lib().mfc_rk3_stage(ctx, int(stage), q_in, q_n, q_out, float(dt), stream))
+
+
 def mfc_rk3_run(ctx, q, nsteps, dt, dt_log, stream) -> None:
     _err(ctx, lib().mfc_rk3_run(ctx, q, int(nsteps), float(dt), dt_log, stream))
 
@@ -201,7 +206,8 @@ class Solver:
                  ghost: int = 3, precision: int = MFC_FP64, weno: int = MFC_WENO_M,
                  weno_eps: Optional[float] = None, cfl: float = 0.4, teno_ct: float = 1e-6,
                  model: int = MFC_MODEL_K0, riemann: int = MFC_RIEMANN_HLLC,
-                 low_mach: int = MFC_LOW_MACH_NONE, eta: Optional[Sequence[float]] = None, device=None):
+                 low_mach: int = MFC_LOW_MACH_NONE, eta: Optional[Sequence[float]] = None,
+                 viscous_dt: bool = False, device=None):
         nd = len(n)
         self.ndim, self.nf = nd, len(gamma)
         self.n = [int(x) for x in n] + [1] * (3 - nd)
@@ -232,6 +238,7 @@ class Solver:
         o.model = int(model)
         o.riemann = int(riemann)
         o.low_mach = int(low_mach)
+        o.viscous_dt = int(bool(viscous_dt))
         with torch.cuda.device(self.device):
             self.ctx = mfc_init(g, e, o)
         self.nq = mfc_num_fields(self.ctx)
@@ -245,7 +252,7 @@ class Solver:
         return cls(case.n, case.gamma, case.pi_inf, lo=case.lo, hi=case.hi, bc_lo=case.bc_lo,
                    bc_hi=case.bc_hi, weno=case.weno, weno_eps=case.eps, cfl=case.cfl, teno_ct=case.teno_ct,
                    model=case.model, riemann=case.riemann, low_mach=case.low_mach,
-                   eta=getattr(case, "eta", None), **kw)
+                   eta=getattr(case, "eta", None), viscous_dt=getattr(case, "viscous_dt", False), **kw)
 
     # layout helpers
     def empty(self) -> torch.Tensor:
@@ -307,6 +314,13 @@ class Solver:
         self._check(q)
         mfc_rk3_step(self.ctx, _ptr(q), dt, _ptr(dt_used), self._stream())
         return q
+
+    def rk3_stage(self, stage: int, q_in: torch.Tensor, q_n: Optional[torch.Tensor], q_out: torch.Tensor,
+                  dt: float) -> torch.Tensor:
+        """Stage 1, 2 or 3 of the RK3 step at the step's dt > 0 (mfc_rk3_stage)."""
+        self._check(q_in, q_n, q_out)
+        mfc_rk3_stage(self.ctx, stage, _ptr(q_in), _ptr(q_n), _ptr(q_out), dt, self._stream())
+        return q_out
 
     def rk3_run(self, q: torch.Tensor, nsteps: int, dt: float = 0.0,
                 dt_log: Optional[torch.Tensor] = None) -> torch.Tensor:

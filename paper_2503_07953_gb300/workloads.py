@@ -46,6 +46,7 @@ class Case:
     riemann: int = 0          # 0: HLLC; 1: HLL
     low_mach: int = 0         # 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC)
     eta: Optional[List[float]] = None  # shear viscosity per fluid (Sec. 2.1.1); None: inviscid
+    viscous_dt: bool = False  # the CFL dt also respects the explicit viscous limit
 
     @property
     def ndim(self) -> int:
