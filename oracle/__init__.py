@@ -74,7 +74,7 @@ class _Problem(ctypes.Structure):
         ("gamma", ctypes.c_double * MAXF), ("pi_inf", ctypes.c_double * MAXF),
         ("weno", ctypes.c_int32), ("eps", ctypes.c_double), ("teno_ct", ctypes.c_double),
         ("model", ctypes.c_int32), ("riemann", ctypes.c_int32), ("low_mach", ctypes.c_int32),
-        ("eta", ctypes.c_double * MAXF),
+        ("eta", ctypes.c_double * MAXF), ("viscous_dt", ctypes.c_int32),
     ]
 
 
@@ -130,6 +130,7 @@ class Problem:
     riemann: int = 0                      # 0: HLLC; 1: HLL
     low_mach: int = 0                     # 0: none; 1: Thornber; 2: anti-dissipation pressure correction
     eta: Sequence[float] = None           # shear viscosity per fluid; None or zeros: inviscid
+    viscous_dt: int = 0                   # 1: the CFL dt also respects the explicit viscous limit
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -169,6 +170,7 @@ class Problem:
             p.eta[i] = float(self.eta[i]) if (self.eta is not None and i < self.nf) else 0.0
         p.weno, p.eps, p.teno_ct = int(self.weno), float(self.eps), float(self.teno_ct)
         p.model, p.riemann, p.low_mach = int(self.model), int(self.riemann), int(self.low_mach)
+        p.viscous_dt = int(self.viscous_dt)
         return p
 
     def dx(self, axis: int) -> float:

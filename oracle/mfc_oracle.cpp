@@ -89,6 +89,7 @@ typedef struct {
     int32_t riemann;  /* 0: HLLC; 1: HLL */
     int32_t low_mach; /* 0: none; 1: Thornber; 2: anti-dissipation pressure correction (HLLC) */
     double eta[MAXF]; /* shear viscosity of each fluid; all zero: inviscid */
+    int32_t viscous_dt; /* 1: the CFL dt also respects the explicit viscous limit */
 } oc_problem;
 }
 
@@ -895,6 +896,22 @@ template <class T> double cfl_dt(const oc_problem& P, const T* q, double cfl) {
             T s = T(dx_of(P, ax)) / (fabs(w[L.mom(ax)]) + cs);
             m = std::min(m, val(s));
         }
+        /* Reading (the paper states no viscous time-step bound): with
+         * viscous_dt, also the explicit limit of the momentum diffusion,
+         * rho min_d dx_d^2 / (2 ndim eta), eta the mixture viscosity
+         * (1 - sum_j alpha_j) eta_N + sum_j alpha_j eta_j of the cell. */
+        if (P.viscous_dt && eos.viscous) {
+            T sa = T(0.0);
+            for (int j = 0; j < L.nf - 1; ++j) sa = sa + qc[L.alpha(j)];
+            T eta = (T(1.0) - sa) * T(eos.eta[L.nf - 1]);
+            for (int j = 0; j < L.nf - 1; ++j) eta = eta + qc[L.alpha(j)] * T(eos.eta[j]);
+            if (val(eta) > 0.0) {
+                double dx2 = dx_of(P, 0) * dx_of(P, 0);
+                for (int ax = 1; ax < P.ndim; ++ax) dx2 = std::min(dx2, dx_of(P, ax) * dx_of(P, ax));
+                T s = rho * T(dx2) / (T(2.0 * P.ndim) * eta);
+                m = std::min(m, val(s));
+            }
+        }
         (void)nq;
     }
     return cfl * m;
@@ -926,6 +943,7 @@ int check_problem(const oc_problem* P) {
     if (P->low_mach == 2 && P->riemann != 0) return -1;
     for (int i = 0; i < P->nf; ++i)
         if (!(P->eta[i] >= 0.0) || !std::isfinite(P->eta[i])) return -1;
+    if (P->viscous_dt != 0 && P->viscous_dt != 1) return -1;
     return 0;
 }
 

@@ -8,7 +8,7 @@ def oracle_problem(oracle, case):
     return oracle.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
                           bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps,
                           teno_ct=case.teno_ct, model=case.model, riemann=case.riemann,
-                          low_mach=case.low_mach, eta=case.eta)
+                          low_mach=case.low_mach, eta=case.eta, viscous_dt=int(getattr(case, "viscous_dt", 0)))
 
 
 def solver_for(mfc, case, **kw):

@@ -191,3 +191,40 @@ def test_inviscid_unchanged_and_refusals(oracle_lib, mfc_lib, cuda_device):
     with pytest.raises(mfc_lib.MfcError) as ei:
         solver_for(mfc_lib, case)
     assert ei.value.status == mfc_lib.MFC_ERR_ARG
+
+
+VISC_DT_CASES = {
+    # viscosities raised until the explicit viscous bound is the binding one
+    "walled_2d_nf2": lambda: walled_case([14, 11], 2),
+    "walled_3d_nf3": lambda: walled_case([9, 8, 7], 3),
+    "taylor_green_2d": lambda: wl.taylor_green(dims=[16, 12], re=100.0),
+}
+
+
+@pytest.mark.parametrize("name", list(VISC_DT_CASES))
+def test_viscous_dt_limit(oracle_lib, mfc_lib, cuda_device, name):
+    """opts.viscous_dt = 1: the CFL dt also takes the explicit viscous limit
+    rho min_d dx_d^2 / (2 ndim eta), bit for bit with the oracle in MFC_FP64
+    (dt and a 5-step run), to rounding in MFC_FP64_FAST; the bound binds in
+    these cases (the dt is below the convective one)."""
+    case, W = VISC_DT_CASES[name]()
+    case.eta = [(5000.0 if name.startswith("taylor") else 50.0) * e for e in case.eta]
+    case.viscous_dt = True
+    P = oracle_problem(oracle_lib, case)
+    q_o = oracle_lib.prim_to_cons(P, W)
+    dt_o = oracle_lib.cfl_dt(P, q_o, case.cfl)
+    case.viscous_dt = False
+    dt_conv = oracle_lib.cfl_dt(oracle_problem(oracle_lib, case), q_o, case.cfl)
+    case.viscous_dt = True
+    assert dt_o < dt_conv
+    S = solver_for(mfc_lib, case)
+    assert S.compute_dt(S.from_interior(q_o)) == dt_o
+    q = S.from_interior(q_o)
+    dts = torch.zeros(5, dtype=torch.float64, device=cuda_device)
+    S.rk3_run(q, 5, 0.0, dts)
+    S.check()
+    q_end, dts_o = oracle_lib.rk3_run(P, q_o, 5, cfl=case.cfl)
+    assert dts.cpu().tolist() == [float(x) for x in dts_o]
+    assert np.array_equal(to_host(S, q), q_end)
+    F = solver_for(mfc_lib, case, precision=mfc_lib.MFC_FP64_FAST)
+    assert F.compute_dt(F.from_interior(q_o)) == pytest.approx(dt_o, rel=1e-14)
