@@ -38,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2503_07953_gb300 import flops  # noqa: E402
+from paper_2503_07953_gb300 import pipes  # noqa: E402
 from paper_2503_07953_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "WENO5-HLLC cell-updates/s per RK3 step, FP64 vs mixed at stated error; VJP/fwd cost"
@@ -430,6 +431,11 @@ def run_ours(args, world, rank, local):
     except (OSError, KeyError, ValueError, TypeError):
         pass
 
+    fp_src = build.source_fingerprint()
+    clock = clk.get("sm_mhz") or 2070.0
+    rec = pipes.load(args.precision, args.workload, fp_src)
+    roof["pipes"] = pipes.roofline(rec, ncell, t_sweep, clock) if rec else None
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f64+f32",
@@ -466,7 +472,10 @@ def run_ours(args, world, rank, local):
             qo = q0.clone()
             for _ in range(args.warmup):
                 So.rk3_step(qo, 0.0)
+            leg_clocks = ClockSampler(local)
+            leg_clocks.start()
             mso = time_steps(So, qo, args.steps)
+            leg_clk = leg_clocks.stop()
             So.check()
             extras[name] = {"value": ncell * args.steps / (mso / 1e3), "ms_per_step": mso / args.steps,
                             "speedup_vs_" + args.precision: ms / mso,
@@ -476,6 +485,14 @@ def run_ours(args, world, rank, local):
                             "sweep_ms_per_launch": time_sweeps(So, qo, 3)}
             if name != "mixed":
                 extras[name]["bitwise_equal_to_fp64"] = bool(torch.equal(So.interior(qo), S.interior(qref)))
+            # the pipe that bounds this leg's sweeps, and how busy it is
+            # (instruction counts per cell-sweep from an ncu capture of these
+            # sources, the sweep time from CUDA events, the clock sampled
+            # during the leg's timed steps)
+            leg_rec = pipes.load(name, args.workload, fp_src)
+            extras[name]["clocks"] = leg_clk
+            extras[name]["roofline"] = (pipes.roofline(leg_rec, ncell, extras[name]["sweep_ms_per_launch"],
+                                                       leg_clk.get("sm_mhz") or 2070.0) if leg_rec else None)
             if name == "df64":
                 # double-float WENO on the float32 pipes beside the float64
                 # Riemann solve: its algorithmic flop rate against the

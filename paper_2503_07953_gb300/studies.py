@@ -126,15 +126,43 @@ def mixed_error(args) -> None:
            "speedup_mixed": ms_ref / ms_mix})
 
 
+def _stored_derivatives(path: str) -> dict:
+    """J, dt figures and dJ_direction_k of a wall_impulse_jvp_<N>.txt file."""
+    out = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
 def adjoint_study(args) -> None:
     case, W = wl.bubble_collapse_2d(args.n)
     a1 = torch.as_tensor(W[case.nf + case.ndim + 1].copy(), dtype=torch.float64, device="cuda")
     band = ((a1 > 1e-3) & (a1 < 1 - 1e-3)).double()
+    stored = _stored_derivatives(args.compare) if args.compare else None
+    fixed_dts = None
+    if args.dt_from_fp64:
+        # the CFL dt sequence of the bit-exact float64 mode (the oracle's, bit
+        # for bit), held by every precision below
+        S0 = mfc.Solver.from_case(case, precision=mfc.MFC_FP64)
+        q = adj.alpha_to_state(S0, case, W, a1).detach()
+        log = torch.zeros(args.steps, dtype=torch.float64, device="cuda")
+        S0.rk3_run(q, args.steps, 0.0, log)
+        S0.check()
+        fixed_dts = [float(x) for x in log.cpu()]
+        del S0, q
+        torch.cuda.empty_cache()
     for pname, h in zip(args.precisions, args.h):
         S = mfc.Solver.from_case(case, precision=PREC[pname])
         q0 = adj.alpha_to_state(S, case, W, a1).detach()
         t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
-        _, _, dts, _ = adj.rollout_gradient(S, q0, args.steps, lambda n, q: q.sum() * 0.0, 1)
+        if fixed_dts is not None:
+            dts = fixed_dts
+        else:
+            _, _, dts, _ = adj.rollout_gradient(S, q0, args.steps, lambda n, q: q.sum() * 0.0, 1)
         loss = adj.wall_pressure_objective(S, case, dts)
         torch.cuda.synchronize(); t0.record()
         J, gq, _, st = adj.rollout_gradient(S, q0, args.steps, loss, args.snapshots, dts)
@@ -158,23 +186,37 @@ def adjoint_study(args) -> None:
         ms_fwd = t0.elapsed_time(t1)
         gen = torch.Generator(device="cpu").manual_seed(0)
         rel, ads, fds = [], [], []
-        for _ in range(args.directions):
+        ndir = max(args.directions, 2 if stored else 0)
+        for k in range(ndir):
             d = torch.randn(a1.shape, generator=gen, dtype=torch.float64).to(a1.device) * band
             d = d / float(d.abs().max())
-            fd = (J_of(a1 + h * d) - J_of(a1 - h * d)) / (2 * h)
             ad = float((ga * d).sum())
-            rel.append(abs(ad - fd) / abs(fd))
             ads.append(ad)
-            fds.append(fd)
+            if k < args.directions:
+                fd = (J_of(a1 + h * d) - J_of(a1 - h * d)) / (2 * h)
+                rel.append(abs(ad - fd) / abs(fd))
+                fds.append(fd)
         S.check()
+        vs_oracle = None
+        if stored:
+            # the oracle's forward-mode derivatives along the same seeded directions
+            vs_oracle = {"J_oracle": stored.get("J"), "J_rel_diff": abs(J - stored["J"]) / abs(stored["J"]),
+                         "dJ_oracle": [stored[f"dJ_direction_{k}"] for k in range(2)],
+                         "dJ_adjoint": ads[:2],
+                         "dJ_rel_diff": [abs(ads[k] - stored[f"dJ_direction_{k}"]) / abs(stored[f"dJ_direction_{k}"])
+                                         for k in range(2)],
+                         "dt_sum_rel_diff": (abs(sum(dts) - stored["dt_sum"]) / stored["dt_sum"]
+                                             if "dt_sum" in stored else None)}
         _emit({"study": "adjoint", "workload": f"bubble_collapse_2d {args.n}x{args.n}, {args.steps} steps",
                "precision": pname, "J": J, "J_forward_only": J_check, "snapshots": args.snapshots,
                "max_live_snapshots": st.max_live_snapshots, "recomputed_steps": st.advances, "vjp_steps": st.vjps,
                "snapshot_bytes": q0.numel() * 8, "ms_gradient": ms_grad, "ms_forward_with_objective": ms_fwd,
                "gradient_over_forward": ms_grad / ms_fwd, "fd_step": h, "fd_directions": args.directions,
                "grad_abs_sum": float(ga.abs().sum()), "directional_adjoint": ads, "directional_fd": fds,
-               "fd_rel_diff": rel, "fd_rel_diff_max": max(rel),
-               "fd_rel_diff_median": sorted(rel)[len(rel) // 2]})
+               "fd_rel_diff": rel, "fd_rel_diff_max": max(rel) if rel else None,
+               "fd_rel_diff_median": sorted(rel)[len(rel) // 2] if rel else None,
+               "dts": "bit-exact float64 mode's CFL sequence" if fixed_dts is not None else "own CFL sequence",
+               "vs_oracle_forward_mode": vs_oracle})
         del S, q0, gq, ga
         torch.cuda.empty_cache()
 
@@ -235,6 +277,10 @@ def main(argv=None) -> None:
     p.add_argument("--precisions", nargs="+", default=["fp64_fast", "mixed"], choices=sorted(PREC))
     p.add_argument("--h", type=float, nargs="+", default=[1e-6, 1e-3],
                    help="central-difference step per precision (directions are max-normalised)")
+    p.add_argument("--dt-from-fp64", action="store_true",
+                   help="hold the bit-exact float64 mode's CFL dt sequence in every precision")
+    p.add_argument("--compare", default=None,
+                   help="a wall_impulse_jvp_<N>.txt file of oracle forward-mode derivatives to compare with")
     p = sub.add_parser("tube")
     p.add_argument("--n", type=int, default=1000)
     p.add_argument("--steps", type=int, default=200)

@@ -1,5 +1,5 @@
-"""Write wall_impulse_jvp_256.txt: the 2D bubble-collapse wall impulse on
-256 x 256 cells over 500 CFL steps (Sec. 3.5-shaped workload, WENO5-M,
+"""Write wall_impulse_jvp_<N>.txt: the 2D bubble-collapse wall impulse on
+N x N cells over a number of CFL steps (Sec. 3.5-shaped workload, WENO5-M,
 HLLC), its value J and its derivatives along two seeded directions of the
 initial volume fraction, from the oracle alone: a forward run for the dt
 sequence, then the forward-mode (dual-number) derivative of every RK3 step
@@ -7,7 +7,15 @@ at those dts.
 
     J = sum_n dt_n dy sum_j p(q^{n+1})[last x cell, j]
 
-Runs for about 15 minutes single-threaded."""
+    python tests/golden/make_wall_impulse_jvp.py                    # 256 x 256, 500 steps
+    python tests/golden/make_wall_impulse_jvp.py --n 1024 --steps 1800 --openmp
+
+256 x 256 over 500 steps runs for about 15 minutes single-threaded.  At
+1024 x 1024 the collapse's pressure waves need about 1360 steps to reach the
+wall, so the 1800-step file has a wall impulse that depends on the initial
+state; it runs for about 2.5 hours on 8 host threads (--openmp: the
+oracle's OpenMP build, bit for bit the single-threaded one)."""
+import argparse
 import os
 import sys
 
@@ -20,8 +28,6 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle as O  # noqa: E402
 from paper_2503_07953_gb300 import workloads as wl  # noqa: E402
 
-N, STEPS = 256, 500
-
 
 def directions(a1, count=2):
     """Seeded directions supported where 1e-3 < alpha_1 < 1 - 1e-3, max-normalised."""
@@ -33,6 +39,15 @@ def directions(a1, count=2):
 
 
 def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--openmp", action="store_true")
+    args = ap.parse_args()
+    N, STEPS = args.n, args.steps
+    if args.openmp:
+        O.build(openmp=True)
+        O.set_parallel(True)
     case, W = wl.bubble_collapse_2d(N)
     P = O.Problem(n=case.n, gamma=case.gamma, pi_inf=case.pi_inf, lo=case.lo, hi=case.hi,
                   bc_lo=case.bc_lo, bc_hi=case.bc_hi, weno=case.weno, eps=case.eps)
@@ -62,6 +77,10 @@ def main():
         return p, dp
 
     lines = [f"# bubble_collapse_2d {N}x{N}, {STEPS} CFL steps, WENO5-M + HLLC; written by make_wall_impulse_jvp.py"]
+    if STEPS != 500 or N != 256:
+        lines.append(f"dt_first {float(dts[0])!r}")
+        lines.append(f"dt_last {float(dts[-1])!r}")
+        lines.append(f"dt_sum {float(np.sum(dts))!r}")
     J = None
     for k, d in enumerate(directions(a1)):
         dq = (q_of(a1 + d) - q_of(a1 - d)) / 2  # the map alpha -> q is affine
@@ -75,7 +94,7 @@ def main():
         J = tot
         lines.append(f"dJ_direction_{k} {float(dtot)!r}")
     lines.insert(1, f"J {float(J)!r}")
-    with open(os.path.join(HERE, "wall_impulse_jvp_256.txt"), "w") as fh:
+    with open(os.path.join(HERE, f"wall_impulse_jvp_{N}.txt"), "w") as fh:
         fh.write("\n".join(lines) + "\n")
 
 
