@@ -104,8 +104,11 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   inside the float32 range (differences across a stencil below ~1e18);
  *   an overflow is reported as MFC_ERR_NONPHYSICAL.  The adjoint entry
  *   points of an MFC_DF64 context recompute the RK stages with the
- *   double-float sweeps and run the adjoint sweeps in the MFC_FP64_FAST
- *   arithmetic. */
+ *   double-float sweeps; their adjoint sweeps recompute the double-float
+ *   face states and run the reverse of WENO5 in double-float arithmetic as
+ *   well (JS and mapped weights; Z and TENO in the MFC_FP64_FAST
+ *   arithmetic), the reverse of HLLC and of the pressure recovery in the
+ *   MFC_FP64_FAST arithmetic. */
 typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_FP64_FAST = 2, MFC_DF64 = 3 } mfc_precision;
 
 /* WENO weights: Jiang-Shu, mapped (Henrick; Sec. 3.2.1), Z with q = 1 (Sec. 4.2.2),

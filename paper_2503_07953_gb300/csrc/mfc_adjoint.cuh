@@ -200,10 +200,170 @@ __device__ __forceinline__ void weno5_edge_adj(const R* p, const R* beta, const 
     }
 }
 
+// Adjoint of weno5_cell_df with JS or mapped weights (MODE_DF): given the
+// bars vlb, vrb of the left- and right-edge values, the bars of f0..f4, in
+// double-float arithmetic on the float32 pipes, the two edges' weight
+// computations paired in df64x2.  The forward quantities are recomputed with
+// weno5_cell_df's operations, and the branch it takes is differentiated:
+// the stencil of the smallest scaled indicator (t_min), the power-of-two
+// scale (piecewise constant), indicators floored at 2^-120 and the flat
+// branch with ideal weights (both constant).  With
+// c = (sum_r omega_r P_r) / 6 and v = f2 + c per edge:
+//   omega (mapped) = gm / sum gm,  gm_r = N_r prod_{s != r} D_s,
+//   N = w (d (1 + d) + w (w - 3 d)),  D = d^2 + w (1 - 2 d),
+//   w = a / sum a,  a_r = d_r u_r^2,  u_r = t_min / t_r,  t_r = s (eps + beta_r).
+struct WenoBars {
+    double b[5];
+};
+
+static __device__ __noinline__ WenoBars weno5_cell_adj_df(double f0, double f1, double f2, double f3, double f4,
+                                                          double vlb, double vrb, int variant, df64 e) {
+    constexpr df64 c13(13.0 / 12.0), sixth(1.0 / 6.0);
+    const df64 D01 = df_from_f64_bits(f1 - f0), D12 = df_from_f64_bits(f2 - f1);
+    const df64 D23 = df_from_f64_bits(f3 - f2), D34 = df_from_f64_bits(f4 - f3);
+    const df64 a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const df64 g[3] = {df_mulf(D12, 3.0f) - D01, D12 + D23, D34 - df_mulf(D23, 3.0f)};
+    df64 t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = e + (c13 * (a[r] * a[r]) + df_scale(g[r] * g[r], 0.25f));
+    const df64 P[3] = {df_mulf(D12, 5.0f) - df_scale(D01, 2.0f), D12 + df_scale(D23, 2.0f),
+                       df_scale(D23, 4.0f) - D34};
+    const df64 Q[3] = {D01 - df_scale(D12, 4.0f), -(df_scale(D12, 2.0f) + D23),
+                       df_scale(D34, 2.0f) - df_mulf(D23, 5.0f)};
+    const double dR[3] = {0.1, 0.6, 0.3}, dL[3] = {0.3, 0.6, 0.1};
+    const df64x2 cb = dfx2(df_from_f64_bits(vrb), df_from_f64_bits(vlb)) * dfx2(sixth, sixth);
+    df64x2 PQb[3];
+    df64 ab[3] = {df64(0.0), df64(0.0), df64(0.0)}, gb[3] = {df64(0.0), df64(0.0), df64(0.0)};
+    const float th = fmaxf(fmaxf(t[0].hi, t[1].hi), t[2].hi);
+    if (!(th >= 0x1p-120f)) {
+        // ideal weights: only the candidates carry bars
+#pragma unroll
+        for (int r = 0; r < 3; ++r) PQb[r] = cb * dfx2(dR[r], dL[r]);
+    } else {
+        int k = ((__float_as_int(th) >> 23) & 0xff) - 127;
+        k = k > 126 ? 126 : k;
+        const float sc = __int_as_float((127 - k) << 23);
+        df64 ts[3];
+        bool floored[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ts[r] = df_scale(t[r], sc);
+            floored[r] = ts[r].hi < 0x1p-120f;
+            if (floored[r]) ts[r] = df64(0x1p-120f, 0.0f);
+        }
+        const float tmh = fminf(fminf(ts[0].hi, ts[1].hi), ts[2].hi);
+        const int rmin = (ts[0].hi == tmh) ? 0 : ((ts[1].hi == tmh) ? 1 : 2);
+        const df64 tmin = ts[rmin];
+        df64 u[3], its[3];
+        df64x2 w[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            its[r] = df_div(df64(1.0), ts[r]);
+            u[r] = tmin * its[r];
+            const df64 u2 = u[r] * u[r];
+            w[r] = dfx2(dR[r], dL[r]) * dfx2(u2, u2);
+        }
+        const df64x2 inv = df_rcp((w[0] + w[1]) + w[2]);
+        df64x2 wn[3], om[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) om[r] = wn[r] = w[r] * inv;
+        df64x2 Nn[3], Dd[3], inv2;
+        if (variant == WENO_M) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                Nn[r] = wn[r] * (dfx2(dR[r] * (1.0 + dR[r]), dL[r] * (1.0 + dL[r])) +
+                                 wn[r] * (wn[r] - dfx2(3.0 * dR[r], 3.0 * dL[r])));
+                Dd[r] = dfx2(dR[r] * dR[r], dL[r] * dL[r]) + wn[r] * dfx2(1.0 - 2.0 * dR[r], 1.0 - 2.0 * dL[r]);
+            }
+            const df64x2 gm0 = Nn[0] * (Dd[1] * Dd[2]), gm1 = Nn[1] * (Dd[0] * Dd[2]), gm2 = Nn[2] * (Dd[0] * Dd[1]);
+            inv2 = df_rcp((gm0 + gm1) + gm2);
+            om[0] = gm0 * inv2;
+            om[1] = gm1 * inv2;
+            om[2] = gm2 * inv2;
+        }
+        // reverse: c = sum om_r PQ_r (times 1/6, in cb)
+        df64x2 omb[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            omb[r] = cb * dfx2(P[r], Q[r]);
+            PQb[r] = cb * om[r];
+        }
+        df64x2 wb[3];
+        if (variant == WENO_M) {
+            // om = gm / sum gm
+            const df64x2 dot = (omb[0] * om[0] + omb[1] * om[1]) + omb[2] * om[2];
+            df64x2 gmb[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) gmb[r] = (omb[r] - dot) * inv2;
+            // gm_r = N_r prod_{s != r} D_s
+            const df64x2 Nb[3] = {gmb[0] * (Dd[1] * Dd[2]), gmb[1] * (Dd[0] * Dd[2]), gmb[2] * (Dd[0] * Dd[1])};
+            const df64x2 gN[3] = {gmb[0] * Nn[0], gmb[1] * Nn[1], gmb[2] * Nn[2]};
+            const df64x2 Db[3] = {gN[1] * Dd[2] + gN[2] * Dd[1], gN[0] * Dd[2] + gN[2] * Dd[0],
+                                  gN[0] * Dd[1] + gN[1] * Dd[0]};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                // N' = d (1 + d) + w (3 w - 6 d), D' = 1 - 2 d
+                const df64x2 dN = dfx2(dR[r] * (1.0 + dR[r]), dL[r] * (1.0 + dL[r])) +
+                                  wn[r] * (wn[r] * dfx2(3.0, 3.0) - dfx2(6.0 * dR[r], 6.0 * dL[r]));
+                wb[r] = Nb[r] * dN + Db[r] * dfx2(1.0 - 2.0 * dR[r], 1.0 - 2.0 * dL[r]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wb[r] = omb[r];
+        }
+        // wn = w / sum w,  w_r = d_r u_r^2 (both edges feed u_r)
+        const df64x2 dotw = (wb[0] * wn[0] + wb[1] * wn[1]) + wb[2] * wn[2];
+        df64 ub[3], tsb[3];
+        df64 tminb(0.0);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const df64x2 x = ((wb[r] - dotw) * inv) * dfx2(dR[r], dL[r]);
+            const df64 u2b = lane_x(x) + lane_y(x);
+            ub[r] = df_scale(u2b * u[r], 2.0f);
+            // u_r = t_min / ts_r
+            tminb = tminb + ub[r] * its[r];
+            tsb[r] = -((ub[r] * u[r]) * its[r]);
+        }
+        tsb[rmin] = tsb[rmin] + tminb;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const df64 tb = floored[r] ? df64(0.0) : df_scale(tsb[r], sc);
+            // t_r = eps + 13/12 a_r^2 + 1/4 g_r^2
+            ab[r] = tb * (c13 * df_scale(a[r], 2.0f));
+            gb[r] = tb * df_scale(g[r], 0.5f);
+        }
+    }
+    const df64 Pb[3] = {lane_x(PQb[0]), lane_x(PQb[1]), lane_x(PQb[2])};
+    const df64 Qb[3] = {lane_y(PQb[0]), lane_y(PQb[1]), lane_y(PQb[2])};
+    const df64 D01b = ((Qb[0] - df_scale(Pb[0], 2.0f)) - ab[0]) - gb[0];
+    const df64 D12b = ((df_mulf(Pb[0], 5.0f) + Pb[1]) - (df_scale(Qb[0], 4.0f) + df_scale(Qb[1], 2.0f))) +
+                      ((ab[0] + df_mulf(gb[0], 3.0f)) + (gb[1] - ab[1]));
+    const df64 D23b = ((df_scale(Pb[1], 2.0f) + df_scale(Pb[2], 4.0f)) - (Qb[1] + df_mulf(Qb[2], 5.0f))) +
+                      ((ab[1] + gb[1]) - (ab[2] + df_mulf(gb[2], 3.0f)));
+    const df64 D34b = (df_scale(Qb[2], 2.0f) - Pb[2]) + (ab[2] + gb[2]);
+    auto dbl = [](df64 x) { return f64_from_f32_bits(x.hi) + f64_from_f32_bits(x.lo); };
+    const double e01 = dbl(D01b), e12 = dbl(D12b), e23 = dbl(D23b), e34 = dbl(D34b);
+    WenoBars out;
+    out.b[0] = -e01;
+    out.b[1] = e01 - e12;
+    out.b[2] = (e12 - e23) + (vrb + vlb);
+    out.b[3] = e23 - e34;
+    out.b[4] = e34;
+    return out;
+}
+
 // Adjoint of weno5_cell: given the bars of the right-edge value (vrb) and
 // the left-edge value (vlb), add df to fb[0..4].
 template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R ct, R* fb) {
+    if constexpr (MODE == MODE_DF) {
+        if (variant == WENO_JS || variant == WENO_M) {
+            const WenoBars w = weno5_cell_adj_df(f[0], f[1], f[2], f[3], f[4], vlb, vrb, variant, df64(double(eps)));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) fb[i] += w.b[i];
+            return;
+        }
+    }
     const R c13 = R(13.0 / 12.0), c14 = R(0.25);
     const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
     const R A1 = f[1] - R(2) * f[2] + f[3], B1 = f[1] - f[3];

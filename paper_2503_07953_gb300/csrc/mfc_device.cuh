@@ -103,6 +103,48 @@ template <class R> __device__ __forceinline__ R rcp(R x);
 template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
 
+// Sign tests and comparisons of float64 values on their bit patterns, with
+// integer instructions: the float64 compare instructions occupy the float64
+// pipe, which bounds the MODE_FAST and MODE_DF sweeps.  f64_pos, f64_neg and
+// f64_nonneg equal x > 0, x < 0 and x >= 0 for every input, NaN included;
+// f64_lt orders like a < b except that -0 is below +0 and NaN above +inf
+// (it picks the sign of a zero in a minimum; NaN only arises in states that
+// are reported non-physical).
+__device__ __forceinline__ bool f64_pos(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b - 1ULL < 0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool f64_neg(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) ^ 0x8000000000000000ULL;
+    return b - 1ULL < 0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool f64_nonneg(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b <= 0x7ff0000000000000ULL || b == 0x8000000000000000ULL;
+}
+__device__ __forceinline__ long long f64_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool f64_lt(double a, double b) { return f64_key(a) < f64_key(b); }
+
+// The comparisons of the sweeps by arithmetic mode: on bit patterns for the
+// float64 values of MODE_FAST and MODE_DF, the compare instructions
+// otherwise (MODE_EXACT keeps the IEEE comparisons the oracle makes).
+template <int MODE, class R> struct Cmp {
+    static __device__ __forceinline__ bool pos(R x) { return x > R(0); }
+    static __device__ __forceinline__ bool neg(R x) { return x < R(0); }
+    static __device__ __forceinline__ bool nonneg(R x) { return x >= R(0); }
+    static __device__ __forceinline__ bool lt(R a, R b) { return a < b; }
+};
+template <> struct Cmp<MODE_FAST, double> {
+    static __device__ __forceinline__ bool pos(double x) { return f64_pos(x); }
+    static __device__ __forceinline__ bool neg(double x) { return f64_neg(x); }
+    static __device__ __forceinline__ bool nonneg(double x) { return f64_nonneg(x); }
+    static __device__ __forceinline__ bool lt(double a, double b) { return f64_lt(a, b); }
+};
+template <> struct Cmp<MODE_DF, double> : Cmp<MODE_FAST, double> {};
+
 // Quotient by arithmetic mode: MODE_EXACT IEEE division; MODE_FAST a times
 // the refined reciprocal of b; MODE_MIXED the fast float32 division.
 template <int MODE> struct Arith {
@@ -198,7 +240,7 @@ __device__ __forceinline__ void cons_to_prim(const double* q, double* w, const C
     double rho = q[0];
 #pragma unroll
     for (int i = 1; i < NF; ++i) rho = rho + q[i];
-    bad |= !(rho > 0.0);
+    bad |= !Cmp<MODE, double>::pos(rho);
 #pragma unroll
     for (int i = 0; i < NF; ++i) w[i] = q[i];
     double u2 = 0.0;
@@ -272,21 +314,43 @@ __device__ __forceinline__ void prim_for_recon(const double* q, R* out, const Co
 
 // A primitive state is a physical mixture when rho > 0, Gamma > 0 and
 // (Gamma + 1) p + Pi > 0 (so that c^2 > 0).
-template <int NF, int ND, class R, int MODE = MODE_EXACT>
-__device__ __forceinline__ bool physical_state(const R* w, const Consts& C) {
+// The mixture quantities of one primitive state that both the physical-state
+// test and the Riemann solver use: rho, Gamma, Pi and num = (Gamma + 1) p + Pi
+// (Gamma rho c^2 of the mixture stiffened gas), computed once per state.
+template <class R>
+struct MixState {
+    R rho, G, P, num;
+};
+
+template <int NF, int ND, int MODE, class R>
+__device__ __forceinline__ MixState<R> mix_state(const R* w, const Consts& C) {
     using L = Lay<NF, ND>;
+    MixState<R> m;
     R rho = w[0];
 #pragma unroll
     for (int i = 1; i < NF; ++i) rho = rho + w[i];
-    R Gamma, Pi;
-    mixture_mode<NF, MODE, R>(w + L::A, C, Gamma, Pi);
-    bool ok = rho > R(0) && Gamma > R(0) && (Gamma + R(1)) * w[L::E] + Pi > R(0);
+    mixture_mode<NF, MODE, R>(w + L::A, C, m.G, m.P);
+    m.rho = rho;
+    m.num = (m.G + R(1)) * w[L::E] + m.P;
+    return m;
+}
+
+template <int NF, int ND, class R, int MODE = MODE_EXACT>
+__device__ __forceinline__ bool physical_mix(const R* w, const MixState<R>& m, const Consts& C) {
+    using L = Lay<NF, ND>;
+    using K = Cmp<MODE, R>;
+    bool ok = K::pos(m.rho) && K::pos(m.G) && K::pos(m.num);
     if constexpr (NF == 2) {
         // Kapila: both phasic impedances gamma_i (p + pi_i) positive
         if (C.model == 1) ok = ok && w[L::E] + phasic<R>(C.pinf, C.pinff, 0) > R(0) &&
                                w[L::E] + phasic<R>(C.pinf, C.pinff, 1) > R(0);
     }
     return ok;
+}
+
+template <int NF, int ND, class R, int MODE = MODE_EXACT>
+__device__ __forceinline__ bool physical_state(const R* w, const Consts& C) {
+    return physical_mix<NF, ND, R, MODE>(w, mix_state<NF, ND, MODE, R>(w, C), C);
 }
 
 // ---------------------------------------------------------------------------
@@ -697,8 +761,12 @@ __device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f
 // one instruction for both edges (FADD2 / FMUL2 / FFMA2).
 __device__ __forceinline__ float2 pair(float r, float l) { return make_float2(r, l); }
 
-__device__ __forceinline__ void weno5_cell_mixed32(float f0, float f1, float f2, float f3, float f4, int variant,
-                                                   float eps, float& vl, float& vr) {
+//
+// Not inlined: one copy of its code serves the N_q fields of a cell from the
+// instruction cache (inlined, the sweeps' loop bodies stalled on instruction
+// fetch); the edge values come back in registers.
+static __device__ __noinline__ float2 weno5_cell_mixed32(float f0, float f1, float f2, float f3, float f4,
+                                                         int variant, float eps) {
     const float D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
     const float a[3] = {D12 - D01, D23 - D12, D34 - D23};
     const float g[3] = {fmaf(3.0f, D12, -D01), D12 + D23, fmaf(-3.0f, D23, D34)};
@@ -753,9 +821,7 @@ __device__ __forceinline__ void weno5_cell_mixed32(float f0, float f1, float f2,
     const float2 c1 = __ffma2_rn(pair(3.0f, -3.0f), pair(g[1], g[1]), pair(a[1], a[1]));
     const float2 c2 = __ffma2_rn(pair(-3.0f, 3.0f), pair(g[2], g[2]), pair(a[2], a[2]));
     const float2 sum = __ffma2_rn(w2, c2, __ffma2_rn(w1, c1, __fmul2_rn(w0, c0)));
-    const float2 v = __ffma2_rn(inv, sum, pair(f2, f2));
-    vr = v.x;
-    vl = v.y;
+    return __ffma2_rn(inv, sum, pair(f2, f2));  // (right edge, left edge)
 }
 
 template <int MODE, class R>
@@ -766,9 +832,19 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
             return;
         }
     }
+    if constexpr (MODE == MODE_DF) {
+        // the double-float reconstruction (the adjoint sweeps recompute the
+        // forward face states of a double-float step with it)
+        const WenoEdges ed = weno5_cell_df(f0, f1, f2, f3, f4, variant, df64(double(eps)), df64(double(ct)));
+        vl = ed.vl;
+        vr = ed.vr;
+        return;
+    }
     if constexpr (MODE == MODE_MIXED) {
         if (variant != WENO_TENO) {
-            weno5_cell_mixed32(f0, f1, f2, f3, f4, variant, eps, vl, vr);
+            const float2 v = weno5_cell_mixed32(f0, f1, f2, f3, f4, variant, eps);
+            vr = v.x;
+            vl = v.y;
             return;
         }
     }
@@ -838,7 +914,8 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
 // the volume-fraction slots receive alpha_K uf.  bad is set when a squared
 // sound speed is not positive.
 template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
-__device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C, R* F, R& uf, bool& bad) {
+__device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const MixState<R>& mL, const MixState<R>& mR,
+                                     const Consts& C, R* F, R& uf, bool& bad) {
     using L = Lay<NF, ND>;
     using A = Arith<MODE>;
     constexpr int NQ = L::NQ;
@@ -846,20 +923,20 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
     // sound speeds of the reconstructed states (independent of the velocity)
     R rho[2], un[2], p[2], E[2], c[2], Gm[2], Pm[2];
     const R* W0[2] = {WL0, WR0};
+    const MixState<R>* M0[2] = {&mL, &mR};
 #pragma unroll
     for (int K = 0; K < 2; ++K) {
         const R* w = W0[K];
-        R r = w[0];
-#pragma unroll
-        for (int i = 1; i < NF; ++i) r = r + w[i];
-        mixture_mode<NF, MODE, R>(w + L::A, C, Gm[K], Pm[K]);
+        const R r = M0[K]->rho;
+        Gm[K] = M0[K]->G;
+        Pm[K] = M0[K]->P;
         rho[K] = r;
         p[K] = w[L::E];
-        R c2 = A::quot((Gm[K] + R(1)) * p[K] + Pm[K], Gm[K] * r);
+        R c2 = A::quot(M0[K]->num, Gm[K] * r);
         if constexpr (NF == 2) {
             if (C.model == 1) c2 = wood_c2<MODE, R>(r, p[K], w[L::A], C);
         }
-        bad |= !(c2 > R(0));
+        bad |= !Cmp<MODE, R>::pos(c2);
         c[K] = sqrt(c2);
     }
     // low-Mach corrections (Sec. 4.2.4): z = min(max(|u_L|/c_L, |u_R|/c_R), 1);
@@ -893,10 +970,11 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
         un[K] = w[UN];
         E[K] = Gm[K] * p[K] + Pm[K] + R(0.5) * rho[K] * u2;
     }
+    using Kc = Cmp<MODE, R>;
     const R aL = un[0] - c[0], aR = un[1] - c[1];
-    const R SL = (aR < aL) ? aR : aL;
+    const R SL = Kc::lt(aR, aL) ? aR : aL;
     const R bL = un[0] + c[0], bR = un[1] + c[1];
-    const R SR = (bR > bL) ? bR : bL;
+    const R SR = Kc::lt(bL, bR) ? bR : bL;
 
     if (C.riemann == 1) {
         // HLL (Sec. 3.2.2): F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)
@@ -926,11 +1004,11 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
                 UK[K][L::A + j] = w[L::A + j];
             }
         }
-        if (SL >= R(0)) {
+        if (Kc::nonneg(SL)) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) F[k] = FK[0][k];
             uf = un[0];
-        } else if (SR <= R(0)) {
+        } else if (!Kc::pos(SR)) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) F[k] = FK[1][k];
             uf = un[1];
@@ -946,14 +1024,14 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
     const R Ss = A::quot(p[1] - p[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]),
                          rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]));
 
-    const bool left = Ss >= R(0);
+    const bool left = Kc::nonneg(Ss);
     const R* w = left ? WL : WR;
     const R rK = left ? rho[0] : rho[1];
     const R uK = left ? un[0] : un[1];
     const R pK = left ? p[0] : p[1];
     const R EK = left ? E[0] : E[1];
     const R SK = left ? SL : SR;
-    const bool star = left ? (SL < R(0)) : (SR > R(0));
+    const bool star = left ? Kc::neg(SL) : Kc::pos(SR);
 
     if constexpr (MODE != MODE_EXACT) {
         // The same star-state fluxes with one reciprocal.  With
@@ -1032,6 +1110,13 @@ __device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C
 #pragma unroll
         for (int j = 0; j < NF - 1; ++j) F[L::A + j] = w[L::A + j] * uf;
     }
+}
+
+// hllc with the mixture quantities of both states computed here.
+template <int NF, int ND, int DIR, int MODE, class R = typename ModeT<MODE>::R>
+__device__ __forceinline__ void hllc(const R* WL0, const R* WR0, const Consts& C, R* F, R& uf, bool& bad) {
+    hllc<NF, ND, DIR, MODE, R>(WL0, WR0, mix_state<NF, ND, MODE, R>(WL0, C), mix_state<NF, ND, MODE, R>(WR0, C), C, F,
+                               uf, bad);
 }
 
 // Index of the interior cell that supplies the value of cell c along an

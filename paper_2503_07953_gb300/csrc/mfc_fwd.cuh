@@ -107,15 +107,18 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
         }
         if (m >= s0) {
             // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)
-            if (!physical_state<NF, ND, R, MODE>(WLprev, C) || !physical_state<NF, ND, R, MODE>(WRm, C)) {
+            MixState<R> mL = mix_state<NF, ND, MODE, R>(WLprev, C), mR = mix_state<NF, ND, MODE, R>(WRm, C);
+            if (!physical_mix<NF, ND, R, MODE>(WLprev, mL, C) || !physical_mix<NF, ND, R, MODE>(WRm, mR, C)) {
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     WLprev[k] = R(W[1][k]);
                     WRm[k] = R(W[2][k]);
                 }
+                mL = mix_state<NF, ND, MODE, R>(WLprev, C);
+                mR = mix_state<NF, ND, MODE, R>(WRm, C);
             }
             R F[NQ], uf;
-            hllc<NF, ND, DIR, MODE>(WLprev, WRm, C, F, uf, bad);
+            hllc<NF, ND, DIR, MODE>(WLprev, WRm, mL, mR, C, F, uf, bad);
             if (m >= s0 + 1) {
                 // finish cell m - 1 = window slot 1: faces m - 3/2 (Fprev) and m - 1/2 (F)
                 const int64_t off = base + (m - 1) * S;
@@ -316,15 +319,18 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
         for (int k = 0; k < NQ; ++k)
             weno5_cell<MODE_MIXED, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
         if (m >= s0) {
-            if (!physical_state<NF, ND, R, MODE_MIXED>(WLprev, C) || !physical_state<NF, ND, R, MODE_MIXED>(WRm, C)) {
+            MixState<R> mL = mix_state<NF, ND, MODE_MIXED, R>(WLprev, C), mR = mix_state<NF, ND, MODE_MIXED, R>(WRm, C);
+            if (!physical_mix<NF, ND, R, MODE_MIXED>(WLprev, mL, C) || !physical_mix<NF, ND, R, MODE_MIXED>(WRm, mR, C)) {
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
                     WLprev[k] = W[1][k];
                     WRm[k] = W[2][k];
                 }
+                mL = mix_state<NF, ND, MODE_MIXED, R>(WLprev, C);
+                mR = mix_state<NF, ND, MODE_MIXED, R>(WRm, C);
             }
             R F[NQ], uf;
-            hllc<NF, ND, DIR, MODE_MIXED>(WLprev, WRm, C, F, uf, bad);
+            hllc<NF, ND, DIR, MODE_MIXED>(WLprev, WRm, mL, mR, C, F, uf, bad);
             if (m >= s0 + 1) {
                 // finish cell m - 1 (window slot 1); its accumulator and q^n are
                 // in update slot g, its state in state slot g - 3
@@ -475,16 +481,19 @@ __device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A
             WR[k] = VL[k];
         }
         const bool face = c >= s0 && c <= s1;
-        if (!physical_state<NF, ND, R, MODE>(WL, C) || !physical_state<NF, ND, R, MODE>(WR, C)) {
+        MixState<R> mL = mix_state<NF, ND, MODE, R>(WL, C), mR = mix_state<NF, ND, MODE, R>(WR, C);
+        if (!physical_mix<NF, ND, R, MODE>(WL, mL, C) || !physical_mix<NF, ND, R, MODE>(WR, mR, C)) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 WL[k] = Wm1[k];
                 WR[k] = Wc[k];
             }
+            mL = mix_state<NF, ND, MODE, R>(WL, C);
+            mR = mix_state<NF, ND, MODE, R>(WR, C);
         }
         R F[NQ], uf;
         bool fb = false;
-        hllc<NF, ND, 0, MODE>(WL, WR, C, F, uf, fb);
+        hllc<NF, ND, 0, MODE>(WL, WR, mL, mR, C, F, uf, fb);
         bad |= face && fb;
         // finish cell c - 1 from faces c - 3/2 (lane - 1) and c - 1/2 (own)
         const R ufm = chunk_neighbour(ufp, uf, uf, lane, -1);

@@ -197,6 +197,8 @@ cudaError_t sweep_vjp_nd(const Consts& C, int dir, int mode, VjpArgs A, cudaStre
         } else {
             if (mode == MODE_MIXED)
                 launch_sweep_vjp<NF, ND, D, MODE_MIXED>(grid, C, A, s);
+            else if (mode == MODE_DF)
+                launch_sweep_vjp<NF, ND, D, MODE_DF>(grid, C, A, s);
             else
                 launch_sweep_vjp<NF, ND, D, MODE_FAST>(grid, C, A, s);
         }

@@ -126,12 +126,16 @@ __global__ void __launch_bounds__(128) riemann_kernel_df(const Consts C, const S
         double WRm[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) WRm[k] = K.E[edge_index(2 * k, m, n, l, K.nl)];
-        if (!physical_state<NF, ND, double, MODE_DF>(WLprev, C) || !physical_state<NF, ND, double, MODE_DF>(WRm, C)) {
+        MixState<double> mL = mix_state<NF, ND, MODE_DF, double>(WLprev, C);
+        MixState<double> mR = mix_state<NF, ND, MODE_DF, double>(WRm, C);
+        if (!physical_mix<NF, ND, double, MODE_DF>(WLprev, mL, C) || !physical_mix<NF, ND, double, MODE_DF>(WRm, mR, C)) {
             prim(m - 1, WLprev);
             prim(m, WRm);
+            mL = mix_state<NF, ND, MODE_DF, double>(WLprev, C);
+            mR = mix_state<NF, ND, MODE_DF, double>(WRm, C);
         }
         double F[NQ], uf;
-        hllc<NF, ND, DIR, MODE_DF>(WLprev, WRm, C, F, uf, bad);
+        hllc<NF, ND, DIR, MODE_DF>(WLprev, WRm, mL, mR, C, F, uf, bad);
         if (m >= s0 + 1) {
             // finish cell m - 1: faces m - 3/2 (Fprev) and m - 1/2 (F)
             const int64_t off = base + (m - 1) * S;

@@ -100,7 +100,9 @@ CASES = {
 }
 SMOOTH = ["smooth_3d_mixed_bc", "smooth_2d_periodic", "stiff_smooth_2d", "smooth_2d_teno", "smooth_2d_kapila",
           "smooth_2d_hll_thornber", "smooth_2d_apc"]
-PARAMS = [(name, 0) for name in sorted(CASES)] + [(name, 2) for name in SMOOTH]
+# MFC_DF64: the adjoint sweeps of a double-float context run the reverse
+# WENO5 in double-float (JS and mapped weights; the other variants in float64)
+PARAMS = [(name, 0) for name in sorted(CASES)] + [(name, 2) for name in SMOOTH] + [(name, 3) for name in SMOOTH]
 
 
 def dot(a, b):
@@ -179,6 +181,21 @@ def test_rhs_full_jacobian(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi,
     q = oracle_lib.prim_to_cons(P, W)
     J, JT = full_jacobians(oracle_lib, S, P, q)
     assert np.abs(JT - J).max() <= 1e-12 * np.abs(J).max()
+
+
+@pytest.mark.parametrize("weno", [0, 1])
+@pytest.mark.parametrize("dims,bc_lo,bc_hi", [((17,), (2,), (2,)), ((19,), (0,), (0,)), ((6, 5), (0, 2), (0, 1))])
+def test_rhs_full_jacobian_df64(oracle_lib, mfc_lib, cuda_device, dims, bc_lo, bc_hi, weno):
+    """The double-float adjoint (reverse WENO5 in double-float arithmetic,
+    48-bit significand) against the oracle's dual numbers, entry by entry:
+    within 1e-10 of the Jacobian's largest entry."""
+    case, W = smooth_case(dims, bc_lo, bc_hi)
+    case.weno, case.eps = weno, (1e-6 if weno == 0 else 1e-40)
+    P = oracle_problem(oracle_lib, case)
+    S = solver_for(mfc_lib, case, precision=mfc_lib.MFC_DF64)
+    q = oracle_lib.prim_to_cons(P, W)
+    J, JT = full_jacobians(oracle_lib, S, P, q)
+    assert np.abs(JT - J).max() <= 1e-10 * np.abs(J).max()
 
 
 @pytest.mark.parametrize("name,weno", [("water_air", 1), ("water_air", 0), ("bubble", 1), ("bubble", 0),
