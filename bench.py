@@ -416,25 +416,17 @@ def run_ours(args, world, rank, local):
     except (OSError, KeyError, ValueError):
         pass
     hbm_ach = 8 * case.nq * 8 * ncell / ((ms / args.steps) / 1e3) / 1e9
-    # DRAM traffic of the sweep kernel from an ncu capture of these very
-    # sources (profiles/sweep_traffic.json), scaled by cells; null otherwise
-    try:
-        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
-            records = json.load(fh)
-        fp = build.source_fingerprint()
-        for tr in (records if isinstance(records, list) else [records]):
-            if (tr["source_fingerprint"] == fp and tr["precision"] == args.precision
-                    and tr["workload"] == args.workload):
-                roof["traffic"] = tr["dram_bytes_per_cell_per_launch"] * ncell
-                roof["traffic_basis"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the x, y, z "
-                                         f"sweeps at {tr['captured']}, scaled by cells")
-    except (OSError, KeyError, ValueError, TypeError):
-        pass
-
+    # DRAM traffic and pipe counts of the sweep kernels from an ncu capture of
+    # these very sources (profiles/sweep_pipes.json), scaled by cells; null
+    # when the sources differ from the captured ones
     fp_src = build.source_fingerprint()
     clock = clk.get("sm_mhz") or 2070.0
     rec = pipes.load(args.precision, args.workload, fp_src)
     roof["pipes"] = pipes.roofline(rec, ncell, t_sweep, clock) if rec else None
+    if rec:
+        roof["traffic"] = rec["dram_bytes_per_cell"] * ncell
+        roof["traffic_basis"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per cell-sweep at "
+                                 f"{rec['captured']}, scaled by cells")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -489,6 +481,12 @@ def run_ours(args, world, rank, local):
             # (instruction counts per cell-sweep from an ncu capture of these
             # sources, the sweep time from CUDA events, the clock sampled
             # during the leg's timed steps)
+            if name in ("df64", "mixed"):
+                # the adjoint step of this precision against its forward step
+                dto = So.compute_dt(qo)
+                ms_f = time_steps(So, qo.clone(), 2) / 2
+                ms_v = time_vjp(So, qo, dto, 2)
+                extras[name]["vjp"] = {"ms_per_step_vjp": ms_v, "ms_per_step_fwd": ms_f, "vjp_over_fwd": ms_v / ms_f}
             leg_rec = pipes.load(name, args.workload, fp_src)
             extras[name]["clocks"] = leg_clk
             extras[name]["roofline"] = (pipes.roofline(leg_rec, ncell, extras[name]["sweep_ms_per_launch"],
