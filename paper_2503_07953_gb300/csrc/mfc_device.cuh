@@ -687,15 +687,18 @@ static __device__ __noinline__ WenoEdges weno5_cell_df(double f0, double f1, dou
 // other two stencils' denominators; Z d_r (t_r + tau) prod_{s != r} t_s.
 // The mapped weights of the two edges sum to within [5e-6, 3] each, so their
 // normalisations share one reciprocal.
-__device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f2, double f3, double f4, int variant,
-                                                  double eps, double& vl, double& vr) {
-    const double D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
-    const double a[3] = {D12 - D01, D23 - D12, D34 - D23};
+// The part of weno5_cell_fast64 that is not shared with the neighbouring
+// cells: from the centre value f2, the differences D01 .. D34, the second
+// differences a_r and the partial indicators A_r = (13/3) a_r^2 + 4 eps
+// (which a march along a line carries over from the previous cell, shifted
+// by one stencil).
+__device__ __forceinline__ void weno5_fast64_core(double f2, double D01, double D12, double D23, double D34,
+                                                  const double* a, const double* A, int variant, double& vl,
+                                                  double& vr) {
     const double g[3] = {fma(3.0, D12, -D01), D12 + D23, fma(-3.0, D23, D34)};
-    const double e4 = 4.0 * eps;
     double t[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) t[r] = fma(g[r], g[r], fma((13.0 / 3.0) * a[r], a[r], e4));
+    for (int r = 0; r < 3; ++r) t[r] = fma(g[r], g[r], A[r]);
     const double cR[3] = {fma(3.0, g[0], a[0]), fma(3.0, g[1], a[1]), fma(-3.0, g[2], a[2])};
     const double cL[3] = {fma(-3.0, g[0], a[0]), fma(-3.0, g[1], a[1]), fma(3.0, g[2], a[2])};
     double wR[3], wL[3], nR, nL;
@@ -750,6 +753,19 @@ __device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f
     const double sL = fma(wL[2], cL[2], fma(wL[1], cL[1], wL[0] * cL[0]));
     vr = fma(iR, sR, f2);
     vl = fma(iL, sL, f2);
+}
+
+// (13/3) a^2 + 4 eps, the part of 4 (eps + beta_r) that depends on the
+// second difference alone
+__device__ __forceinline__ double weno5_fast64_A(double a, double e4) { return fma((13.0 / 3.0) * a, a, e4); }
+
+__device__ __forceinline__ void weno5_cell_fast64(double f0, double f1, double f2, double f3, double f4, int variant,
+                                                  double eps, double& vl, double& vr) {
+    const double D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
+    const double a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const double e4 = 4.0 * eps;
+    const double A[3] = {weno5_fast64_A(a[0], e4), weno5_fast64_A(a[1], e4), weno5_fast64_A(a[2], e4)};
+    weno5_fast64_core(f2, D01, D12, D23, D34, a, A, variant, vl, vr);
 }
 
 // MODE_MIXED WENO5 of one cell (JS, mapped and Z weights) in float32: the

@@ -63,6 +63,38 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
 #pragma unroll
     for (int k = 0; k < 4; ++k) load_prim(s0 - 3 + k, W[k]);
 
+    // MODE_FAST with JS, mapped or Z weights: the differences D_j, second
+    // differences a_r and partial indicators A_r of a cell's stencil
+    // (weno5_fast64_core) are the previous cell's shifted by one, so each
+    // thread keeps three D, two a and two A per field in shared-memory rings
+    // ([slot][field][thread]) and computes only those of the new cell; the
+    // values are those weno5_cell_fast64 would compute, bit for bit.
+    constexpr bool kSlide = MODE == MODE_FAST;
+    const bool slide = kSlide && variant != WENO_TENO;
+    extern __shared__ double slide_ring[];
+    auto RD = [&](int slot, int k) -> double& { return slide_ring[(slot * NQ + k) * blockDim.x + threadIdx.x]; };
+    auto RA = [&](int slot, int k) -> double& { return slide_ring[((3 + slot) * NQ + k) * blockDim.x + threadIdx.x]; };
+    auto RB = [&](int slot, int k) -> double& { return slide_ring[((5 + slot) * NQ + k) * blockDim.x + threadIdx.x]; };
+    int d0 = 0, d1 = 1, d2 = 2, p0 = 0, p1 = 1;  // ring slots of D01, D12, D23 and of a0, a1
+    const double e4 = 4.0 * C.eps;
+    if constexpr (kSlide) {
+        if (slide) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                const double D01 = double(W[1][k]) - double(W[0][k]), D12 = double(W[2][k]) - double(W[1][k]);
+                const double D23 = double(W[3][k]) - double(W[2][k]);
+                const double a0 = D12 - D01, a1 = D23 - D12;
+                RD(0, k) = D01;
+                RD(1, k) = D12;
+                RD(2, k) = D23;
+                RA(0, k) = a0;
+                RA(1, k) = a1;
+                RB(0, k) = weno5_fast64_A(a0, e4);
+                RB(1, k) = weno5_fast64_A(a1, e4);
+            }
+        }
+    }
+
     R WLprev[NQ], Fprev[NQ], uprev = R(0);
     const double dtv = (A.out_kind != 0) ? *A.dt : 0.0;
 
@@ -94,16 +126,42 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
         }
         load_prim(m + 2, W[4]);
         R WRm[NQ], WLm[NQ];
+        if constexpr (kSlide) {
+            if (slide) {
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            if constexpr (MODE == MODE_DF) {
-                const WenoEdges e = weno5_cell_df(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps_df,
-                                                  ct_df);
-                WRm[k] = e.vl;
-                WLm[k] = e.vr;
-                bad |= e.bad != 0;
-            } else
-                weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
+                for (int k = 0; k < NQ; ++k) {
+                    const double D01 = RD(d0, k), D12 = RD(d1, k), D23 = RD(d2, k);
+                    const double D34 = double(W[4][k]) - double(W[3][k]);
+                    const double a[3] = {RA(p0, k), RA(p1, k), D34 - D23};
+                    const double Ab[3] = {RB(p0, k), RB(p1, k), weno5_fast64_A(a[2], e4)};
+                    weno5_fast64_core(double(W[2][k]), D01, D12, D23, D34, a, Ab, variant, WRm[k], WLm[k]);
+                    // the new cell's values replace the oldest
+                    RD(d0, k) = D34;
+                    RA(p0, k) = a[2];
+                    RB(p0, k) = Ab[2];
+                }
+                const int t = d0;
+                d0 = d1;
+                d1 = d2;
+                d2 = t;
+                p0 ^= 1;
+                p1 ^= 1;
+            }
+        }
+        if (!(kSlide && slide)) {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                if constexpr (MODE == MODE_DF) {
+                    const WenoEdges e = weno5_cell_df(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps_df,
+                                                      ct_df);
+                    WRm[k] = e.vl;
+                    WLm[k] = e.vr;
+                    bad |= e.bad != 0;
+                } else {
+                    weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k],
+                                        WLm[k]);
+                }
+            }
         }
         if (m >= s0) {
             // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)

@@ -31,12 +31,26 @@ inline unsigned stride_grid(int64_t n, int block) {
     return (unsigned)b;
 }
 
+// Dynamic shared memory of the MODE_FAST march: the rings of sliding WENO5
+// quantities, 7 doubles per field and thread (sweep_body).
+template <int NF, int ND>
+constexpr int slide_smem_bytes(int block) {
+    return 7 * Lay<NF, ND>::NQ * 8 * block;
+}
+
 template <int NF, int ND, int DIR, int MODE>
 void launch_sweep(unsigned grid, const Consts& C, const SweepArgs& A, cudaStream_t s) {
-    if constexpr (MODE == MODE_MIXED)
+    if constexpr (MODE == MODE_MIXED) {
         sweep_kernel_mixed<NF, ND, DIR><<<grid, kSweepBlock, 0, s>>>(C, A);
-    else
+    } else if constexpr (MODE == MODE_FAST) {
+        constexpr int smem = slide_smem_bytes<NF, ND>(kSweepBlock);
+        static const cudaError_t attr = cudaFuncSetAttribute(sweep_kernel<NF, ND, DIR, MODE>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        (void)attr;
+        sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, smem, s>>>(C, A);
+    } else {
         sweep_kernel<NF, ND, DIR, MODE><<<grid, kSweepBlock, 0, s>>>(C, A);
+    }
 }
 
 // y and z sweeps of the mixed mode with shared-memory staging
