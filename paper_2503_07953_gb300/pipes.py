@@ -78,12 +78,13 @@ def counts_from_rows(rows: list, cells: int, sweeps: int) -> dict:
         lid = r["ID"]
         kname = r["Kernel Name"].split("(")[0].split("<")[0].strip()
         if name == "gpu__time_duration.sum":
-            scale = {"nsecond": 1.0, "usecond": 1e3, "msecond": 1e6, "second": 1e9}.get(unit, 1.0)
+            scale = {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6,
+                     "s": 1e9, "second": 1e9}[unit]
             k = kernels.setdefault(kname, {"launches": 0, "ns": 0.0})
             k["launches"] += 1
             k["ns"] += val * scale
         if name.startswith("dram__bytes"):
-            scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1.0)
+            scale = {"byte": 1.0, "Kbyte": 1e3, "KB": 1e3, "Mbyte": 1e6, "MB": 1e6, "Gbyte": 1e9, "GB": 1e9}[unit]
             val *= scale
         if name.endswith(".sum"):
             tot[name] = tot.get(name, 0.0) + val
