@@ -352,18 +352,373 @@ static __device__ __noinline__ WenoBars weno5_cell_adj_df(double f0, double f1, 
     return out;
 }
 
+// Adjoint of weno5_cell_fast64 (JS, mapped and Z weights; MODE_FAST): the
+// bars of f0..f4 given the bars vlb, vrb of the left- and right-edge values,
+// in weno5_cell_fast64's own formulation, so that the indicators, the
+// unnormalised weights and their products are formed once for both edges
+// and each normalisation costs one reciprocal.  Per edge, with y_r the
+// final unnormalised weights, n' = sum y, i = 1 / (12 n') and c_r the
+// scaled candidate corrections (12 (candidate_r - f2)):
+//   v = f2 + i sum_r y_r c_r,
+//   y_bar_r = v_bar i (c_r - 12 i sum_s y_s c_s),  c_bar_r = v_bar i y_r;
+// mapped: y_r = N_r D_s D_q ({r, s, q} = {0, 1, 2}) with N = x (x (x - 3 d)
+// + d (1 + d)), D = x (1 - 2 d) + d^2, x = w / sum w, so
+//   N_bar_r = y_bar_r D_s D_q,  D_bar_r = sum_{s != r} y_bar_s N_s D_q,
+//   x_bar_r = N_bar_r (3 x^2 - 6 d x + d (1 + d)) + D_bar_r (1 - 2 d),
+//   w_bar_r = (x_bar_r - sum_s x_bar_s x_s) / sum w;
+// JS and Z: y = w.  Both edges' w are d_r P_r (d = (1, 6, 3)/10 right,
+// (3, 6, 1)/10 left), so P_bar_r = dR_r w_bar^R_r + dL_r w_bar^L_r, and
+// from P_r = prod_{s != r} t_s^2 (JS, mapped) or (t_r + tau) prod_{s != r}
+// t_s, tau = |t_0 - t_2| (Z) to t_r = g_r^2 + (13/3) a_r^2 + 4 eps and the
+// candidates c^R_r = a_r + 3 s_r g_r, c^L_r = a_r - 3 s_r g_r (s = +1, +1,
+// -1), back to the consecutive differences and f.  The function has no
+// branch but tau's sign (taken as the forward's |.| takes it: +1 at 0).
+// Not inlined: one copy of its code serves the N_q fields from the
+// instruction cache.
+static __device__ __noinline__ WenoBars weno5_cell_adj_fast64(double f0, double f1, double f2, double f3,
+                                                              double f4, double vlb, double vrb, int variant,
+                                                              double eps) {
+    const double D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
+    const double a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const double e4 = 4.0 * eps;
+    const double g[3] = {fma(3.0, D12, -D01), D12 + D23, fma(-3.0, D23, D34)};
+    double t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = fma(g[r], g[r], weno5_fast64_A(a[r], e4));
+    const double cs[2][3] = {{fma(3.0, g[0], a[0]), fma(3.0, g[1], a[1]), fma(-3.0, g[2], a[2])},
+                             {fma(-3.0, g[0], a[0]), fma(-3.0, g[1], a[1]), fma(3.0, g[2], a[2])}};
+    const double ds[2][3] = {{0.1, 0.6, 0.3}, {0.3, 0.6, 0.1}};
+    // unnormalised JS / Z weights d_r P_r
+    double s[3], P[3], Q[3], tau = 0.0;
+    if (variant == WENO_Z) {
+        tau = fabs(t[0] - t[2]);
+        Q[0] = t[1] * t[2];
+        Q[1] = t[0] * t[2];
+        Q[2] = t[0] * t[1];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) P[r] = (t[r] + tau) * Q[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) s[r] = t[r] * t[r];
+        P[0] = s[1] * s[2];
+        P[1] = s[0] * s[2];
+        P[2] = s[0] * s[1];
+    }
+    const double m1 = 0.6 * P[1];
+    double w[2][3] = {{0.1 * P[0], m1, 0.3 * P[2]}, {0.3 * P[0], m1, 0.1 * P[2]}};
+    double y[2][3], n[2], iw[2] = {0.0, 0.0};
+    double x[2][3], N[2][3], D[2][3];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        n[e] = (w[e][0] + w[e][1]) + w[e][2];
+        if (variant == WENO_M) {
+            const double* d = ds[e];
+            iw[e] = rcp_nr(n[e]);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                x[e][r] = w[e][r] * iw[e];
+                N[e][r] = x[e][r] * fma(x[e][r], x[e][r] - 3.0 * d[r], d[r] * (1.0 + d[r]));
+                D[e][r] = fma(x[e][r], 1.0 - 2.0 * d[r], d[r] * d[r]);
+            }
+            y[e][0] = N[e][0] * (D[e][1] * D[e][2]);
+            y[e][1] = N[e][1] * (D[e][0] * D[e][2]);
+            y[e][2] = N[e][2] * (D[e][0] * D[e][1]);
+            n[e] = (y[e][0] + y[e][1]) + y[e][2];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) y[e][r] = w[e][r];
+        }
+    }
+    double in[2];
+    if (variant == WENO_M) {
+        // the mapped sums lie within [5e-6, 3]: one reciprocal for both edges
+        const double rr = rcp_nr((12.0 * n[0]) * n[1]);
+        in[0] = n[1] * rr;
+        in[1] = n[0] * rr;
+    } else {
+        in[0] = rcp_nr(12.0 * n[0]);
+        in[1] = rcp_nr(12.0 * n[1]);
+    }
+    // reverse, edge by edge: bars of the candidates and of w
+    const double vb[2] = {vrb, vlb};
+    double cb[2][3], wb[2][3];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const double m = vb[e] * in[e];
+        const double* c = cs[e];
+        const double u = in[e] * fma(y[e][2], c[2], fma(y[e][1], c[1], y[e][0] * c[0]));
+        const double mh = m * (12.0 * u);
+        double yb[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            yb[r] = fma(m, c[r], -mh);
+            cb[e][r] = m * y[e][r];
+        }
+        if (variant == WENO_M) {
+            const double* d = ds[e];
+            const double* Ne = N[e];
+            const double* De = D[e];
+            const double Nb[3] = {yb[0] * (De[1] * De[2]), yb[1] * (De[0] * De[2]), yb[2] * (De[0] * De[1])};
+            const double YN[3] = {yb[0] * Ne[0], yb[1] * Ne[1], yb[2] * Ne[2]};
+            const double Db[3] = {fma(YN[1], De[2], YN[2] * De[1]), fma(YN[0], De[2], YN[2] * De[0]),
+                                  fma(YN[0], De[1], YN[1] * De[0])};
+            double xb[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double dN = fma(x[e][r], fma(3.0, x[e][r], -6.0 * d[r]), d[r] * (1.0 + d[r]));
+                xb[r] = fma(Db[r], 1.0 - 2.0 * d[r], Nb[r] * dN);
+            }
+            const double dot = fma(xb[2], x[e][2], fma(xb[1], x[e][1], xb[0] * x[e][0]));
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wb[e][r] = (xb[r] - dot) * iw[e];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) wb[e][r] = yb[r];
+        }
+    }
+    // w^R_r = dR_r P_r, w^L_r = dL_r P_r
+    const double Pb[3] = {fma(0.1, wb[0][0], 0.3 * wb[1][0]), 0.6 * (wb[0][1] + wb[1][1]),
+                          fma(0.3, wb[0][2], 0.1 * wb[1][2])};
+    double tb[3];
+    if (variant == WENO_Z) {
+        // P_r = (t_r + tau) Q_r, Q_r = prod_{s != r} t_s
+        const double PE[3] = {Pb[0] * (t[0] + tau), Pb[1] * (t[1] + tau), Pb[2] * (t[2] + tau)};
+        tb[0] = fma(Pb[0], Q[0], fma(PE[1], t[2], PE[2] * t[1]));
+        tb[1] = fma(Pb[1], Q[1], fma(PE[0], t[2], PE[2] * t[0]));
+        tb[2] = fma(Pb[2], Q[2], fma(PE[0], t[1], PE[1] * t[0]));
+        const double taub = fma(Pb[2], Q[2], fma(Pb[1], Q[1], Pb[0] * Q[0]));
+        // tau = |t_0 - t_2|, d|z|/dz = +1 at 0
+        const double sg = (f64_nonneg(t[0] - t[2])) ? taub : -taub;
+        tb[0] += sg;
+        tb[2] -= sg;
+    } else {
+        // P_0 = s_1 s_2, P_1 = s_0 s_2, P_2 = s_0 s_1, s_r = t_r^2
+        const double sb[3] = {fma(Pb[1], s[2], Pb[2] * s[1]), fma(Pb[0], s[2], Pb[2] * s[0]),
+                              fma(Pb[0], s[1], Pb[1] * s[0])};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) tb[r] = (t[r] + t[r]) * sb[r];
+    }
+    // t_r = g_r^2 + (13/3) a_r^2 + 4 eps; c^R_r = a_r + 3 s_r g_r, c^L_r = a_r - 3 s_r g_r
+    double ab[3], gb[3];
+    const double sgn[3] = {3.0, 3.0, -3.0};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        ab[r] = fma((26.0 / 3.0) * a[r], tb[r], cb[0][r] + cb[1][r]);
+        gb[r] = fma(g[r] + g[r], tb[r], sgn[r] * (cb[0][r] - cb[1][r]));
+    }
+    // a_0 = D12 - D01, a_1 = D23 - D12, a_2 = D34 - D23;
+    // g_0 = 3 D12 - D01, g_1 = D12 + D23, g_2 = D34 - 3 D23
+    const double D01b = -(ab[0] + gb[0]);
+    const double D12b = (ab[0] - ab[1]) + fma(3.0, gb[0], gb[1]);
+    const double D23b = (ab[1] - ab[2]) + fma(-3.0, gb[2], gb[1]);
+    const double D34b = ab[2] + gb[2];
+    WenoBars out;
+    out.b[0] = -D01b;
+    out.b[1] = D01b - D12b;
+    out.b[2] = (D12b - D23b) + (vrb + vlb);
+    out.b[3] = D23b - D34b;
+    out.b[4] = D34b;
+    return out;
+}
+
+// Adjoint of weno5_cell_mixed32 (JS, mapped and Z weights; MODE_MIXED):
+// weno5_cell_adj_fast64's reverse in float32, the two edges' weight
+// arithmetic paired in float2 instructions as in the forward.  The forward
+// evaluates the weights on t_r = b_r s + e, b_r = 4 beta_r, s = 1 / sum b,
+// e = max(4 eps s, 1e-9), and the reverse differentiates that map too:
+// dt_s/db_r = s (delta_rs - t_s + e_f) with e_f = e where the floor is taken
+// and 0 where e = 4 eps s, so b_bar_r = s (t_bar_r - sum_s t_bar_s (t_s - e_f)).
+struct WenoBars32 {
+    float b[5];
+};
+
+static __device__ __noinline__ WenoBars32 weno5_cell_adj_mixed32(float f0, float f1, float f2, float f3, float f4,
+                                                                 float vlb, float vrb, int variant, float eps) {
+    const float D01 = f1 - f0, D12 = f2 - f1, D23 = f3 - f2, D34 = f4 - f3;
+    const float a[3] = {D12 - D01, D23 - D12, D34 - D23};
+    const float g[3] = {fmaf(3.0f, D12, -D01), D12 + D23, fmaf(-3.0f, D23, D34)};
+    float b[3];  // 4 beta_r
+#pragma unroll
+    for (int r = 0; r < 3; ++r) b[r] = fmaf((13.0f / 3.0f) * a[r], a[r], g[r] * g[r]);
+    const float scale = __fdividef(1.0f, (b[0] + b[1]) + (b[2] + 4e-30f));
+    const float e0 = 4.0f * eps * scale;
+    const bool floored = !(e0 > 1e-9f);
+    const float e = fmaxf(e0, 1e-9f);
+    float t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = fmaf(b[r], scale, e);
+    float P[3], Q[3], s[3], tau = 0.0f;
+    if (variant == WENO_Z) {
+        tau = fabsf(t[0] - t[2]);
+        Q[0] = t[1] * t[2];
+        Q[1] = t[0] * t[2];
+        Q[2] = t[0] * t[1];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) P[r] = (t[r] + tau) * Q[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) s[r] = t[r] * t[r];
+        P[0] = s[1] * s[2];
+        P[1] = s[0] * s[2];
+        P[2] = s[0] * s[1];
+    }
+    // (right, left) pairs: ideal weights, unnormalised weights
+    const float2 d[3] = {pair(0.1f, 0.3f), pair(0.6f, 0.6f), pair(0.3f, 0.1f)};
+    float2 y[3], x[3], N[3], E[3], EE[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) y[r] = __fmul2_rn(d[r], pair(P[r], P[r]));
+    float2 nrm = __fadd2_rn(__fadd2_rn(y[0], y[1]), y[2]);
+    float2 iw = pair(0.0f, 0.0f);
+    if (variant == WENO_M) {
+        iw = pair(__fdividef(1.0f, nrm.x), __fdividef(1.0f, nrm.y));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = __fmul2_rn(y[r], iw);
+        // N = x (x (x - 3 d) + d (1 + d)), E = x (1 - 2 d) + d^2
+        N[0] = __fmul2_rn(x[0], __ffma2_rn(x[0], __fadd2_rn(x[0], pair(-0.3f, -0.9f)), pair(0.11f, 0.39f)));
+        N[1] = __fmul2_rn(x[1], __ffma2_rn(x[1], __fadd2_rn(x[1], pair(-1.8f, -1.8f)), pair(0.96f, 0.96f)));
+        N[2] = __fmul2_rn(x[2], __ffma2_rn(x[2], __fadd2_rn(x[2], pair(-0.9f, -0.3f)), pair(0.39f, 0.11f)));
+        E[0] = __ffma2_rn(x[0], pair(0.8f, 0.4f), pair(0.01f, 0.09f));
+        E[1] = __ffma2_rn(x[1], pair(-0.2f, -0.2f), pair(0.36f, 0.36f));
+        E[2] = __ffma2_rn(x[2], pair(0.4f, 0.8f), pair(0.09f, 0.01f));
+        EE[0] = __fmul2_rn(E[1], E[2]);
+        EE[1] = __fmul2_rn(E[0], E[2]);
+        EE[2] = __fmul2_rn(E[0], E[1]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) y[r] = __fmul2_rn(N[r], EE[r]);
+        nrm = __fadd2_rn(__fadd2_rn(y[0], y[1]), y[2]);
+    }
+    const float2 in = pair(__fdividef(1.0f, 12.0f * nrm.x), __fdividef(1.0f, 12.0f * nrm.y));
+    const float2 c[3] = {__ffma2_rn(pair(3.0f, -3.0f), pair(g[0], g[0]), pair(a[0], a[0])),
+                         __ffma2_rn(pair(3.0f, -3.0f), pair(g[1], g[1]), pair(a[1], a[1])),
+                         __ffma2_rn(pair(-3.0f, 3.0f), pair(g[2], g[2]), pair(a[2], a[2]))};
+    // reverse: v = f2 + in sum_r y_r c_r per edge
+    const float2 m = __fmul2_rn(pair(vrb, vlb), in);
+    const float2 u = __fmul2_rn(in, __ffma2_rn(y[2], c[2], __ffma2_rn(y[1], c[1], __fmul2_rn(y[0], c[0]))));
+    const float2 mh = __fmul2_rn(m, __fmul2_rn(pair(12.0f, 12.0f), u));
+    const float2 nmh = pair(-mh.x, -mh.y);
+    float2 yb[3], cb[3], wb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        yb[r] = __ffma2_rn(m, c[r], nmh);
+        cb[r] = __fmul2_rn(m, y[r]);
+    }
+    if (variant == WENO_M) {
+        const float2 YN[3] = {__fmul2_rn(yb[0], N[0]), __fmul2_rn(yb[1], N[1]), __fmul2_rn(yb[2], N[2])};
+        const float2 Eb[3] = {__ffma2_rn(YN[1], E[2], __fmul2_rn(YN[2], E[1])),
+                              __ffma2_rn(YN[0], E[2], __fmul2_rn(YN[2], E[0])),
+                              __ffma2_rn(YN[0], E[1], __fmul2_rn(YN[1], E[0]))};
+        // N' = x (3 x - 6 d) + d (1 + d); E' = 1 - 2 d
+        const float2 m6d[3] = {pair(-0.6f, -1.8f), pair(-3.6f, -3.6f), pair(-1.8f, -0.6f)};
+        const float2 d1d[3] = {pair(0.11f, 0.39f), pair(0.96f, 0.96f), pair(0.39f, 0.11f)};
+        const float2 dE[3] = {pair(0.8f, 0.4f), pair(-0.2f, -0.2f), pair(0.4f, 0.8f)};
+        float2 xb[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float2 dN = __ffma2_rn(x[r], __ffma2_rn(pair(3.0f, 3.0f), x[r], m6d[r]), d1d[r]);
+            xb[r] = __ffma2_rn(Eb[r], dE[r], __fmul2_rn(__fmul2_rn(yb[r], EE[r]), dN));
+        }
+        const float2 dot = __ffma2_rn(xb[2], x[2], __ffma2_rn(xb[1], x[1], __fmul2_rn(xb[0], x[0])));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) wb[r] = __fmul2_rn(__fadd2_rn(xb[r], pair(-dot.x, -dot.y)), iw);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) wb[r] = yb[r];
+    }
+    // w^R_r = dR_r P_r, w^L_r = dL_r P_r
+    float Pb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float2 q = __fmul2_rn(wb[r], d[r]);
+        Pb[r] = q.x + q.y;
+    }
+    float tb[3];
+    if (variant == WENO_Z) {
+        const float PE[3] = {Pb[0] * (t[0] + tau), Pb[1] * (t[1] + tau), Pb[2] * (t[2] + tau)};
+        tb[0] = fmaf(Pb[0], Q[0], fmaf(PE[1], t[2], PE[2] * t[1]));
+        tb[1] = fmaf(Pb[1], Q[1], fmaf(PE[0], t[2], PE[2] * t[0]));
+        tb[2] = fmaf(Pb[2], Q[2], fmaf(PE[0], t[1], PE[1] * t[0]));
+        const float taub = fmaf(Pb[2], Q[2], fmaf(Pb[1], Q[1], Pb[0] * Q[0]));
+        const float sg = (t[0] - t[2] >= 0.0f) ? taub : -taub;
+        tb[0] += sg;
+        tb[2] -= sg;
+    } else {
+        const float sb[3] = {fmaf(Pb[1], s[2], Pb[2] * s[1]), fmaf(Pb[0], s[2], Pb[2] * s[0]),
+                             fmaf(Pb[0], s[1], Pb[1] * s[0])};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) tb[r] = (t[r] + t[r]) * sb[r];
+    }
+    // t_s = b_s s + e
+    const float ef = floored ? e : 0.0f;
+    const float corr = fmaf(tb[2], t[2] - ef, fmaf(tb[1], t[1] - ef, tb[0] * (t[0] - ef)));
+    float ab[3], gb[3];
+    const float sgn[3] = {3.0f, 3.0f, -3.0f};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float bb = scale * (tb[r] - corr);
+        // b_r = (13/3) a_r^2 + g_r^2; c^R_r = a_r + 3 s_r g_r, c^L_r = a_r - 3 s_r g_r
+        ab[r] = fmaf((26.0f / 3.0f) * a[r], bb, cb[r].x + cb[r].y);
+        gb[r] = fmaf(g[r] + g[r], bb, sgn[r] * (cb[r].x - cb[r].y));
+    }
+    const float D01b = -(ab[0] + gb[0]);
+    const float D12b = (ab[0] - ab[1]) + fmaf(3.0f, gb[0], gb[1]);
+    const float D23b = (ab[1] - ab[2]) + fmaf(-3.0f, gb[2], gb[1]);
+    const float D34b = ab[2] + gb[2];
+    WenoBars32 out;
+    out.b[0] = -D01b;
+    out.b[1] = D01b - D12b;
+    out.b[2] = (D12b - D23b) + (vrb + vlb);
+    out.b[3] = D23b - D34b;
+    out.b[4] = D34b;
+    return out;
+}
+
+// x != 0 for every x, NaN included; for float64 on the bit pattern (integer
+// instructions, off the float64 pipe).
+template <class R> __device__ __forceinline__ bool nonzero(R x) { return x != R(0); }
+template <> __device__ __forceinline__ bool nonzero<double>(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ULL;
+}
+
 // Adjoint of weno5_cell: given the bars of the right-edge value (vrb) and
-// the left-edge value (vlb), add df to fb[0..4].
+// the left-edge value (vlb), write df to fb[0..4].
 template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell_adj(const R* f, R vlb, R vrb, int variant, R eps, R ct, R* fb) {
+    if constexpr (MODE == MODE_FAST) {
+        if (variant != WENO_TENO) {
+            if (!nonzero(vlb) && !nonzero(vrb)) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) fb[i] = R(0);
+                return;
+            }
+            const WenoBars w = weno5_cell_adj_fast64(f[0], f[1], f[2], f[3], f[4], vlb, vrb, variant, eps);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) fb[i] = w.b[i];
+            return;
+        }
+    }
+    if constexpr (MODE == MODE_MIXED) {
+        if (variant != WENO_TENO) {
+            if (vlb == R(0) && vrb == R(0)) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) fb[i] = R(0);
+                return;
+            }
+            const WenoBars32 w = weno5_cell_adj_mixed32(f[0], f[1], f[2], f[3], f[4], vlb, vrb, variant, eps);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) fb[i] = w.b[i];
+            return;
+        }
+    }
     if constexpr (MODE == MODE_DF) {
         if (variant == WENO_JS || variant == WENO_M) {
             const WenoBars w = weno5_cell_adj_df(f[0], f[1], f[2], f[3], f[4], vlb, vrb, variant, df64(double(eps)));
 #pragma unroll
-            for (int i = 0; i < 5; ++i) fb[i] += w.b[i];
+            for (int i = 0; i < 5; ++i) fb[i] = w.b[i];
             return;
         }
     }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) fb[i] = R(0);
     const R c13 = R(13.0 / 12.0), c14 = R(0.25);
     const R A0 = f[0] - R(2) * f[1] + f[2], B0 = f[0] - R(4) * f[1] + R(3) * f[2];
     const R A1 = f[1] - R(2) * f[2] + f[3], B1 = f[1] - f[3];

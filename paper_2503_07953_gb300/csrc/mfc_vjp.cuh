@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                     // the face states are the cell states themselves
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
-                        if (WLb[k] != R(0)) sink(j, k, WLb[k]);
-                        if (WRb[k] != R(0)) sink(j + 1, k, WRb[k]);
+                        if (nonzero(WLb[k])) sink(j, k, WLb[k]);
+                        if (nonzero(WRb[k])) sink(j + 1, k, WRb[k]);
                         WLb[k] = WRb[k] = R(0);
                     }
                 }
@@ -224,13 +224,13 @@ __global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const Vjp
                 // left edge = face j-1 (WRbprev)
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    R f[5], fb[5] = {R(0), R(0), R(0), R(0), R(0)};
+                    R f[5], fb[5];
 #pragma unroll
                     for (int m = 0; m < 5; ++m) f[m] = WR(j - 2 + m, k);
                     weno5_cell_adj<MODE, R>(f, WRbprev[k], WLb[k], variant, eps, ct, fb);
 #pragma unroll
                     for (int m = 0; m < 5; ++m)
-                        if (fb[m] != R(0)) sink(j - 2 + m, k, fb[m]);
+                        if (nonzero(fb[m])) sink(j - 2 + m, k, fb[m]);
                 }
             }
             // finish cell j-3
