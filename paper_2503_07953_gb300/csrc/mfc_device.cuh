@@ -842,6 +842,102 @@ static __device__ __noinline__ float2 weno5_cell_mixed32(float f0, float f1, flo
     return __ffma2_rn(inv, sum, pair(f2, f2));  // (right edge, left edge)
 }
 
+// weno5_cell_mixed32 of two fields A and B at once (JS, mapped and Z
+// weights): the per-field scalar steps (differences, indicators and their
+// scaling, the products P_r) run as float2 instructions on the pair (A, B),
+// and each field's edge-paired weights follow as in weno5_cell_mixed32, the
+// two fields' chains interleaved.  Every lane performs the single-field
+// function's operations with the same roundings (x - y as fma(y, -1, x) is
+// the same rounded difference), so the results are bit for bit those of two
+// weno5_cell_mixed32 calls.  Not inlined, like weno5_cell_mixed32.
+struct WenoPair32 {
+    float2 a, b;  // (right edge, left edge) of fields A and B
+};
+
+__device__ __forceinline__ float2 fsub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.0f, -1.0f), x); }
+
+// The edge-paired weights and edge values of one field from its P_r, the
+// differences' a_r and g_r, and the centre value f2.
+__device__ __forceinline__ float2 weno5_mixed32_edges(float P0, float P1, float P2, float a0, float a1, float a2,
+                                                      float g0, float g1, float g2, float f2, int variant) {
+    const float2 d0 = pair(0.1f, 0.3f), d1 = pair(0.6f, 0.6f), d2 = pair(0.3f, 0.1f);
+    float2 w0 = __fmul2_rn(d0, pair(P0, P0));
+    float2 w1 = __fmul2_rn(d1, pair(P1, P1));
+    float2 w2 = __fmul2_rn(d2, pair(P2, P2));
+    float2 nrm = __fadd2_rn(__fadd2_rn(w0, w1), w2);
+    float2 inv;
+    if (variant == WENO_M) {
+        inv = pair(__fdividef(1.0f, nrm.x), __fdividef(1.0f, nrm.y));
+        const float2 x0 = __fmul2_rn(w0, inv), x1 = __fmul2_rn(w1, inv), x2 = __fmul2_rn(w2, inv);
+        const float2 N0 = __fmul2_rn(x0, __ffma2_rn(x0, __fadd2_rn(x0, pair(-0.3f, -0.9f)), pair(0.11f, 0.39f)));
+        const float2 N1 = __fmul2_rn(x1, __ffma2_rn(x1, __fadd2_rn(x1, pair(-1.8f, -1.8f)), pair(0.96f, 0.96f)));
+        const float2 N2 = __fmul2_rn(x2, __ffma2_rn(x2, __fadd2_rn(x2, pair(-0.9f, -0.3f)), pair(0.39f, 0.11f)));
+        const float2 E0 = __ffma2_rn(x0, pair(0.8f, 0.4f), pair(0.01f, 0.09f));
+        const float2 E1 = __ffma2_rn(x1, pair(-0.2f, -0.2f), pair(0.36f, 0.36f));
+        const float2 E2 = __ffma2_rn(x2, pair(0.4f, 0.8f), pair(0.09f, 0.01f));
+        w0 = __fmul2_rn(N0, __fmul2_rn(E1, E2));
+        w1 = __fmul2_rn(N1, __fmul2_rn(E0, E2));
+        w2 = __fmul2_rn(N2, __fmul2_rn(E0, E1));
+        nrm = __fadd2_rn(__fadd2_rn(w0, w1), w2);
+    }
+    inv = pair(__fdividef(1.0f, 12.0f * nrm.x), __fdividef(1.0f, 12.0f * nrm.y));
+    const float2 c0 = __ffma2_rn(pair(3.0f, -3.0f), pair(g0, g0), pair(a0, a0));
+    const float2 c1 = __ffma2_rn(pair(3.0f, -3.0f), pair(g1, g1), pair(a1, a1));
+    const float2 c2 = __ffma2_rn(pair(-3.0f, 3.0f), pair(g2, g2), pair(a2, a2));
+    const float2 sum = __ffma2_rn(w2, c2, __ffma2_rn(w1, c1, __fmul2_rn(w0, c0)));
+    return __ffma2_rn(inv, sum, pair(f2, f2));
+}
+
+static __device__ __noinline__ WenoPair32 weno5_cells_mixed32_x2(float fa0, float fa1, float fa2, float fa3,
+                                                                 float fa4, float fb0, float fb1, float fb2,
+                                                                 float fb3, float fb4, int variant, float eps) {
+    const float2 F0 = pair(fa0, fb0), F1 = pair(fa1, fb1), F2 = pair(fa2, fb2), F3 = pair(fa3, fb3),
+                 F4 = pair(fa4, fb4);
+    // -D01 (= f0 - f1, the same rounding as -(f1 - f0)), D12, D23, D34
+    const float2 nD01 = fsub2(F0, F1), D12 = fsub2(F2, F1), D23 = fsub2(F3, F2), D34 = fsub2(F4, F3);
+    const float2 a[3] = {__fadd2_rn(D12, nD01), fsub2(D23, D12), fsub2(D34, D23)};
+    const float2 g[3] = {__ffma2_rn(pair(3.0f, 3.0f), D12, nD01), __fadd2_rn(D12, D23),
+                         __ffma2_rn(pair(-3.0f, -3.0f), D23, D34)};
+    float2 b[3];  // 4 beta_r
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        b[r] = __ffma2_rn(__fmul2_rn(pair(13.0f / 3.0f, 13.0f / 3.0f), a[r]), a[r], __fmul2_rn(g[r], g[r]));
+    const float2 den = __fadd2_rn(__fadd2_rn(b[0], b[1]), __fadd2_rn(b[2], pair(4e-30f, 4e-30f)));
+    const float2 scale = pair(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    const float e4 = 4.0f * eps;
+    const float2 e0 = __fmul2_rn(pair(e4, e4), scale);
+    const float2 e = pair(fmaxf(e0.x, 1e-9f), fmaxf(e0.y, 1e-9f));
+    float2 t[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t[r] = __ffma2_rn(b[r], scale, e);
+    float2 P[3];
+    if (variant == WENO_Z) {
+        const float2 dt = fsub2(t[0], t[2]);
+        const float2 tau = pair(fabsf(dt.x), fabsf(dt.y));
+        P[0] = __fmul2_rn(__fadd2_rn(t[0], tau), __fmul2_rn(t[1], t[2]));
+        P[1] = __fmul2_rn(__fadd2_rn(t[1], tau), __fmul2_rn(t[0], t[2]));
+        P[2] = __fmul2_rn(__fadd2_rn(t[2], tau), __fmul2_rn(t[0], t[1]));
+    } else {
+        const float2 s0 = __fmul2_rn(t[0], t[0]), s1 = __fmul2_rn(t[1], t[1]), s2 = __fmul2_rn(t[2], t[2]);
+        P[0] = __fmul2_rn(s1, s2);
+        P[1] = __fmul2_rn(s0, s2);
+        P[2] = __fmul2_rn(s0, s1);
+    }
+    WenoPair32 out;
+    out.a = weno5_mixed32_edges(P[0].x, P[1].x, P[2].x, a[0].x, a[1].x, a[2].x, g[0].x, g[1].x, g[2].x, fa2, variant);
+    out.b = weno5_mixed32_edges(P[0].y, P[1].y, P[2].y, a[0].y, a[1].y, a[2].y, g[0].y, g[1].y, g[2].y, fb2, variant);
+    return out;
+}
+
+// MODE_MIXED WENO5 of the NQ fields of a cell: f0..f4 the stencil (each
+// [NQ]); vl, vr the left- and right-edge values.  Fields go two at a time
+// through weno5_cells_mixed32_x2 (an odd last one through
+// weno5_cell_mixed32); TENO field by field.
+template <int NQ>
+__device__ __forceinline__ void weno5_fields_mixed32(const float* f0, const float* f1, const float* f2,
+                                                     const float* f3, const float* f4, int variant, float eps,
+                                                     float ct, float* vl, float* vr);
+
 template <int MODE, class R>
 __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int variant, R eps, R ct, R& vl, R& vr) {
     if constexpr (MODE == MODE_FAST) {
@@ -921,6 +1017,32 @@ __device__ __forceinline__ void weno5_cell(R f0, R f1, R f2, R f3, R f4, int var
         const R pl1 = (R(2) * f1 + R(5) * f2 - f3) * sixth;
         const R pl2 = (R(11) * f2 - R(7) * f3 + R(2) * f4) * sixth;
         vl = omL[0] * pl0 + omL[1] * pl1 + omL[2] * pl2;
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void weno5_fields_mixed32(const float* f0, const float* f1, const float* f2,
+                                                     const float* f3, const float* f4, int variant, float eps,
+                                                     float ct, float* vl, float* vr) {
+    if (variant == WENO_TENO) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) weno5_cell<MODE_MIXED, float>(f0[k], f1[k], f2[k], f3[k], f4[k], variant, eps, ct,
+                                                                   vl[k], vr[k]);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < NQ; k += 2) {
+        const WenoPair32 w = weno5_cells_mixed32_x2(f0[k], f1[k], f2[k], f3[k], f4[k], f0[k + 1], f1[k + 1],
+                                                    f2[k + 1], f3[k + 1], f4[k + 1], variant, eps);
+        vr[k] = w.a.x;
+        vl[k] = w.a.y;
+        vr[k + 1] = w.b.x;
+        vl[k + 1] = w.b.y;
+    }
+    if constexpr (NQ % 2 == 1) {
+        const float2 v = weno5_cell_mixed32(f0[NQ - 1], f1[NQ - 1], f2[NQ - 1], f3[NQ - 1], f4[NQ - 1], variant, eps);
+        vr[NQ - 1] = v.x;
+        vl[NQ - 1] = v.y;
     }
 }
 

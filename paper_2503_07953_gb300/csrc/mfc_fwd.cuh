@@ -157,11 +157,13 @@ __device__ __forceinline__ void sweep_body(const Consts& C, const SweepArgs& A) 
                     WRm[k] = e.vl;
                     WLm[k] = e.vr;
                     bad |= e.bad != 0;
-                } else {
+                } else if constexpr (MODE != MODE_MIXED) {
                     weno5_cell<MODE, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k],
                                         WLm[k]);
                 }
             }
+            if constexpr (MODE == MODE_MIXED) weno5_fields_mixed32<NQ>(W[0], W[1], W[2], W[3], W[4], variant, eps, ct,
+                                                                       WRm, WLm);
         }
         if (m >= s0) {
             // face m - 1/2: left state WLprev (cell m-1), right state WRm (cell m)
@@ -262,12 +264,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Shared-memory rings of the staged mixed sweep, per thread: kStageQ slots
 // of the conservative state of one cell, kStageU slots of the accumulator
-// (float) and q^n of one cell, each value at [slot][field][thread].
+// (float) and, for a stage update that reads q^n, kStageU slots of q^n of one
+// cell; each value at [slot][field][thread], q^n's rings last so that the
+// sweeps without them take less shared memory (eight blocks per SM).
 constexpr int kStageQ = 5;
 constexpr int kStageU = 2;
 template <int NQ>
-constexpr int staged_smem_bytes(int block) {
-    return block * (kStageQ * NQ * 8 + kStageU * NQ * (8 + 4));
+constexpr int staged_smem_bytes(int block, bool with_qn) {
+    return block * (kStageQ * NQ * 8 + kStageU * NQ * 4 + (with_qn ? kStageU * NQ * 8 : 0));
 }
 
 // The y and z sweeps of the mixed mode with their global loads staged
@@ -292,8 +296,8 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int bd = blockDim.x, tx = threadIdx.x;
     double* ringQ = reinterpret_cast<double*>(stage_raw);
-    double* ringN = ringQ + kStageQ * NQ * bd;
-    float* ringF = reinterpret_cast<float*>(ringN + kStageU * NQ * bd);
+    float* ringF = reinterpret_cast<float*>(ringQ + kStageQ * NQ * bd);
+    double* ringN = reinterpret_cast<double*>(ringF + kStageU * NQ * bd);  // 8-byte aligned: bd is even
     auto Q = [&](int slot, int f) -> double* { return ringQ + (slot * NQ + f) * bd + tx; };
     auto QN = [&](int slot, int f) -> double* { return ringN + (slot * NQ + f) * bd + tx; };
     auto RF = [&](int slot, int f) -> float* { return ringF + (slot * NQ + f) * bd + tx; };
@@ -373,9 +377,7 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
         cp_async_wait<1>();
         prim_of(g, W[4]);
         R WRm[NQ], WLm[NQ];
-#pragma unroll
-        for (int k = 0; k < NQ; ++k)
-            weno5_cell<MODE_MIXED, R>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], variant, eps, ct, WRm[k], WLm[k]);
+        weno5_fields_mixed32<NQ>(W[0], W[1], W[2], W[3], W[4], variant, eps, ct, WRm, WLm);
         if (m >= s0) {
             MixState<R> mL = mix_state<NF, ND, MODE_MIXED, R>(WLprev, C), mR = mix_state<NF, ND, MODE_MIXED, R>(WRm, C);
             if (!physical_mix<NF, ND, R, MODE_MIXED>(WLprev, mL, C) || !physical_mix<NF, ND, R, MODE_MIXED>(WRm, mR, C)) {
@@ -436,11 +438,11 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
     if (bad) atomicOr(A.flag, 1);
 }
 
-// Seven 64-thread blocks per SM (14 warps): the registers this allows and
-// seven blocks' rings fit one SM; fewer warps left the march's dependency
-// stalls exposed (8 warps: issue active 36-39 %).
+// Eight 64-thread blocks per SM (16 warps) at 128 registers where the rings
+// fit (the sweeps that read no q^n), seven otherwise; fewer warps left the
+// march's dependency stalls exposed (8 warps: issue active 36-39 %).
 template <int NF, int ND, int DIR>
-__global__ void __launch_bounds__(64, 7) sweep_kernel_staged(const Consts C, const SweepArgs A) {
+__global__ void __launch_bounds__(64, 8) sweep_kernel_staged(const Consts C, const SweepArgs A) {
     sweep_body_staged<NF, ND, DIR>(C, A);
 }
 
@@ -522,14 +524,58 @@ __device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A
     while (c0 <= s1) {
         const int64_t c = c0 + lane;
         R VL[NQ], VR[NQ], Wm1[NQ];
+        if constexpr (MODE == MODE_MIXED) {
+            // fields two at a time (weno5_cells_mixed32_x2), an odd last one alone
+            if (variant != WENO_TENO) {
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const R fm2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -2);
-            const R fm1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -1);
-            const R fp1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 1);
-            const R fp2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 2);
-            weno5_cell<MODE, R>(fm2, fm1, Wc[k], fp1, fp2, variant, eps, ct, VL[k], VR[k]);
-            Wm1[k] = fm1;
+                for (int k = 0; k < NQ; k += 2) {
+                    const int k1 = (k + 1 < NQ) ? k + 1 : k;
+                    R fm2[2], fm1[2], fp1[2], fp2[2];
+                    const int nh = (k + 1 < NQ) ? 2 : 1;
+#pragma unroll
+                    for (int h = 0; h < nh; ++h) {
+                        const int kk = h ? k1 : k;
+                        fm2[h] = chunk_neighbour(Wp[kk], Wc[kk], Wn[kk], lane, -2);
+                        fm1[h] = chunk_neighbour(Wp[kk], Wc[kk], Wn[kk], lane, -1);
+                        fp1[h] = chunk_neighbour(Wp[kk], Wc[kk], Wn[kk], lane, 1);
+                        fp2[h] = chunk_neighbour(Wp[kk], Wc[kk], Wn[kk], lane, 2);
+                    }
+                    if (k + 1 < NQ) {
+                        const WenoPair32 w = weno5_cells_mixed32_x2(fm2[0], fm1[0], Wc[k], fp1[0], fp2[0], fm2[1],
+                                                                    fm1[1], Wc[k1], fp1[1], fp2[1], variant, eps);
+                        VR[k] = w.a.x;
+                        VL[k] = w.a.y;
+                        VR[k1] = w.b.x;
+                        VL[k1] = w.b.y;
+                    } else {
+                        const float2 v = weno5_cell_mixed32(fm2[0], fm1[0], Wc[k], fp1[0], fp2[0], variant, eps);
+                        VR[k] = v.x;
+                        VL[k] = v.y;
+                    }
+                    Wm1[k] = fm1[0];
+                    if (k + 1 < NQ) Wm1[k1] = fm1[1];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    const R fm2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -2);
+                    const R fm1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -1);
+                    const R fp1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 1);
+                    const R fp2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 2);
+                    weno5_cell<MODE, R>(fm2, fm1, Wc[k], fp1, fp2, variant, eps, ct, VL[k], VR[k]);
+                    Wm1[k] = fm1;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                const R fm2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -2);
+                const R fm1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, -1);
+                const R fp1 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 1);
+                const R fp2 = chunk_neighbour(Wp[k], Wc[k], Wn[k], lane, 2);
+                weno5_cell<MODE, R>(fm2, fm1, Wc[k], fp1, fp2, variant, eps, ct, VL[k], VR[k]);
+                Wm1[k] = fm1;
+            }
         }
         // face c - 1/2: left state = right edge value of cell c - 1
         R WL[NQ], WR[NQ];
@@ -699,17 +745,26 @@ __global__ void __launch_bounds__(256) cfl_kernel(const Consts C, const double* 
 }
 
 // The CFL reduction in the MODE_FAST arithmetic (MFC_FP64_FAST and
-// MFC_MIXED): one refined reciprocal each for rho, Gamma and the largest
-// (|u_d| + c)/dx_d of the cell, whose reciprocal is min_d dx_d/(|u_d| + c);
-// float64 throughout, same reductions as cfl_kernel.
+// MFC_MIXED): one refined reciprocal each for rho and Gamma per cell; the
+// largest (|u_d| + c)/dx_d over the block's cells is reduced first and its
+// reciprocal, min dx_d/(|u_d| + c), taken once per block.  The maxima of these
+// non-negative doubles and the sign tests run on bit patterns with integer
+// instructions (off the float64 pipe that bounds this kernel); a non-physical
+// state gives NaN, which orders above every finite value here, is ignored by
+// the final minimum (NaN's pattern is above +inf's) and is reported by the
+// flag.  float64 throughout.
 template <int NF, int ND>
 __global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const double* q, unsigned long long* minbits,
                                                        int* flag) {
     using L = Lay<NF, ND>;
     constexpr int NQ = L::NQ;
     const int64_t ncell = C.n[0] * C.n[1] * C.n[2];
-    double m = __longlong_as_double(0x7ff0000000000000ULL);
+    long long mb = 0;  // bit pattern of the largest (|u_d| + c)/dx_d so far (+0.0)
     bool bad = false;
+    auto bmax = [](long long a, double v) {
+        const long long b = __double_as_longlong(v);
+        return b > a ? b : a;
+    };
     for (int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lin < ncell;
          lin += (int64_t)gridDim.x * blockDim.x) {
         const int64_t off = interior_offset(C, lin);
@@ -719,7 +774,7 @@ __global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const dou
         double rho = qc[0];
 #pragma unroll
         for (int i = 1; i < NF; ++i) rho = rho + qc[i];
-        bad |= !(rho > 0.0);
+        bad |= !f64_pos(rho);
         const double irho = rcp_nr(rho);
         double u[ND], ke = 0.0;
 #pragma unroll
@@ -735,38 +790,39 @@ __global__ void __launch_bounds__(256) cfl_fast_kernel(const Consts C, const dou
         if constexpr (NF == 2) {
             if (C.model == 1) c2 = wood_c2<MODE_FAST, double>(rho, p, qc[L::A], C);
         }
-        bad |= !(c2 > 0.0);
+        bad |= !f64_pos(c2);
         const double cs = sqrt(c2);
-        double smax = 0.0;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) smax = fmax(smax, (fabs(u[d]) + cs) * C.inv_dx[d]);
+        for (int d = 0; d < ND; ++d) mb = bmax(mb, (fabs(u[d]) + cs) * C.inv_dx[d]);
         if (C.visc_dt) {
             // the viscous limit's reciprocal, 2 ndim eta / (rho min_d dx_d^2)
             double eta = C.eta[NF - 1];
 #pragma unroll
             for (int j = 0; j < NF - 1; ++j) eta = fma(qc[L::A + j], C.eta[j] - C.eta[NF - 1], eta);
-            smax = fmax(smax, (2.0 * ND) * eta * irho * C.inv_dx2min);
+            mb = bmax(mb, (2.0 * ND) * eta * irho * C.inv_dx2min);
         }
-        const double s = rcp_nr(smax);
-        m = (s < m) ? s : m;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double t = __shfl_down_sync(0xffffffffu, m, o);
-        m = (t < m) ? t : m;
+        const long long t = __shfl_down_sync(0xffffffffu, mb, o);
+        mb = t > mb ? t : mb;
     }
-    __shared__ double wm[8];
+    __shared__ long long wm[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wm[wid] = m;
+    if (lane == 0) wm[wid] = mb;
     __syncthreads();
     if (wid == 0) {
-        m = (lane < (int)(blockDim.x >> 5)) ? wm[lane] : __longlong_as_double(0x7ff0000000000000ULL);
+        mb = (lane < (int)(blockDim.x >> 5)) ? wm[lane] : 0LL;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double t = __shfl_down_sync(0xffffffffu, m, o);
-            m = (t < m) ? t : m;
+            const long long t = __shfl_down_sync(0xffffffffu, mb, o);
+            mb = t > mb ? t : mb;
         }
-        if (lane == 0) atomicMin(minbits, (unsigned long long)__double_as_longlong(m));
+        if (lane == 0) {
+            // min dx_d/(|u_d| + c) of the block (+inf when every maximum is 0)
+            const double m = mb == 0 ? __longlong_as_double(0x7ff0000000000000LL) : rcp_nr(__longlong_as_double(mb));
+            atomicMin(minbits, (unsigned long long)__double_as_longlong(m));
+        }
     }
     if (bad) atomicOr(flag, 1);
 }
