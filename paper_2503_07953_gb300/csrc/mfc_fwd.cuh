@@ -262,29 +262,45 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory rings of the staged mixed sweep, per thread: kStageQ slots
-// of the conservative state of one cell, kStageU slots of the accumulator
-// (float) and, for a stage update that reads q^n, kStageU slots of q^n of one
-// cell; each value at [slot][field][thread], q^n's rings last so that the
-// sweeps without them take less shared memory (eight blocks per SM).
+// float -> double, exact.  The conversion instruction issues to the float64
+// pipe, which the stage updates of the staged sweep already load heavily, so
+// normal floats and zeros are widened with integer instructions on the bit
+// pattern instead (sign; exponent + 1023 - 127; mantissa shifted into the top
+// of the 52-bit field); subnormal, infinite and NaN inputs take the
+// conversion instruction.
+__device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u)
+        return __hiloint2double((int)((b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + 0x38000000u)), (int)(b << 29));
+    if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return double(f);
+}
+
+// Shared memory of the staged mixed sweep, per thread: a ring of kStageQ
+// slots of the conservative state of one cell, then one slot of the
+// accumulator (float) of the cell being finished and, for a stage update
+// that reads q^n, one slot of its q^n; each value at [slot][field][thread].
+// Eight 64-thread blocks fit an SM with or without the q^n slot.
 constexpr int kStageQ = 5;
-constexpr int kStageU = 2;
 template <int NQ>
 constexpr int staged_smem_bytes(int block, bool with_qn) {
-    return block * (kStageQ * NQ * 8 + kStageU * NQ * 4 + (with_qn ? kStageU * NQ * 8 : 0));
+    return block * (kStageQ * NQ * 8 + NQ * 4 + (with_qn ? NQ * 8 : 0));
 }
 
 // The y and z sweeps of the mixed mode with their global loads staged
 // through shared memory.  Each thread marches its line segment exactly as
 // sweep_body<MODE_MIXED> does (same arithmetic in the same order, so the
 // results are identical); its loads are asynchronous copies into per-thread
-// rings, issued one cell ahead of their use: group g holds the state of cell
-// s0 - 3 + g (the window's new cell when g >= 4) and the accumulator and
-// q^n of cell s0 - 6 + g (the cell finished while group g is consumed).  The
-// copies of a warp are contiguous along x, and the march waits only for
-// copies issued an iteration earlier, so the latency of the loads (L2 or
-// HBM) overlaps the reconstruction and Riemann solve of the previous cell
-// instead of stalling the update.  The state of the finished cell, needed
+// shared memory, in two kinds of commit group: S(g), the state of cell
+// s0 - 3 + g (the window's new cell when g >= 4), issued at the top of the
+// iteration before the one that converts it; and U(g), the accumulator and
+// q^n of cell s0 - 6 + g (the cell finished in iteration g), issued at the end
+// of iteration g - 1 into the single slot the update of that iteration has
+// just read.  Iteration g waits for S(g) before its reconstruction and for
+// U(g) before its update, so the latency of the loads (L2 or HBM) overlaps
+// the reconstruction and Riemann solve instead of stalling them.  The copies
+// of a warp are contiguous along x.  The state of the finished cell, needed
 // by the stage update, is still in the state ring (group g - 3).
 template <int NF, int ND, int DIR>
 __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepArgs& A) {
@@ -296,11 +312,11 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
     extern __shared__ __align__(16) unsigned char stage_raw[];
     const int bd = blockDim.x, tx = threadIdx.x;
     double* ringQ = reinterpret_cast<double*>(stage_raw);
-    float* ringF = reinterpret_cast<float*>(ringQ + kStageQ * NQ * bd);
-    double* ringN = reinterpret_cast<double*>(ringF + kStageU * NQ * bd);  // 8-byte aligned: bd is even
+    float* slotF = reinterpret_cast<float*>(ringQ + kStageQ * NQ * bd);
+    double* slotN = reinterpret_cast<double*>(slotF + NQ * bd);  // 8-byte aligned: bd is even
     auto Q = [&](int slot, int f) -> double* { return ringQ + (slot * NQ + f) * bd + tx; };
-    auto QN = [&](int slot, int f) -> double* { return ringN + (slot * NQ + f) * bd + tx; };
-    auto RF = [&](int slot, int f) -> float* { return ringF + (slot * NQ + f) * bd + tx; };
+    auto QN = [&](int f) -> double* { return slotN + f * bd + tx; };
+    auto RF = [&](int f) -> float* { return slotF + f * bd + tx; };
 
     const int64_t nta = C.n[TA], ntb = C.n[TB];
     const int64_t nlines = nta * ntb;
@@ -322,7 +338,8 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
 
     const int64_t G = (s1 - s0) + 6;
     int64_t issued = 0;
-    auto issue = [&]() {
+    // S(issued): the state of cell s0 - 3 + issued into its ring slot
+    auto issue_state = [&]() {
         if (issued < G) {
             const int slot = (int)(issued % kStageQ);
             bool flip = false;
@@ -330,22 +347,25 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
             const double* p = A.q + base + cc * S;
 #pragma unroll
             for (int f = 0; f < NQ; ++f) cp_async8(Q(slot, f), p + f * C.fstride);
-            const int64_t u = s0 - 6 + issued;
-            if (u >= s0 && u < s1) {
-                const int us = (int)(issued % kStageU);
-                const int64_t o = base + u * S;
-                if (acc) {
-#pragma unroll
-                    for (int f = 0; f < NQ; ++f) cp_async4(RF(us, f), A.rhsf + o + f * C.fstride);
-                }
-                if (upd2) {
-#pragma unroll
-                    for (int f = 0; f < NQ; ++f) cp_async8(QN(us, f), A.qn + o + f * C.fstride);
-                }
-            }
         }
         cp_async_commit();
         ++issued;
+    };
+    // U(g): the accumulator and q^n of cell s0 - 6 + g (empty group outside the segment)
+    auto issue_update = [&](int64_t g) {
+        const int64_t u = s0 - 6 + g;
+        if (u >= s0 && u < s1) {
+            const int64_t o = base + u * S;
+            if (acc) {
+#pragma unroll
+                for (int f = 0; f < NQ; ++f) cp_async4(RF(f), A.rhsf + o + f * C.fstride);
+            }
+            if (upd2) {
+#pragma unroll
+                for (int f = 0; f < NQ; ++f) cp_async8(QN(f), A.qn + o + f * C.fstride);
+            }
+        }
+        cp_async_commit();
     };
     // primitive state of the cell of group g, from its ring slot
     auto prim_of = [&](int64_t g, R* out) {
@@ -359,22 +379,23 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
         prim_for_recon<NF, ND, MODE_MIXED, R>(qc, out, C, bad);
     };
 
-    issue();  // group 0; one group is always in flight ahead of the one in use
+    issue_state();  // S(0); one state group is always in flight ahead of the one in use
     R W[5][NQ];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        issue();
+        issue_state();
         cp_async_wait<1>();
         prim_of(k, W[k]);
     }
+    issue_update(4);  // U(4) (empty: no cell is finished in the first iterations)
 
     R WLprev[NQ], Fprev[NQ], uprev = R(0);
     const double dtv = (A.out_kind != 0) ? *A.dt : 0.0;
 
     for (int64_t m = s0 - 1; m <= s1; ++m) {
         const int64_t g = m + 5 - s0;
-        issue();
-        cp_async_wait<1>();
+        issue_state();          // S(g + 1)
+        cp_async_wait<2>();     // S(g) done; U(g) and S(g + 1) may be in flight
         prim_of(g, W[4]);
         R WRm[NQ], WLm[NQ];
         weno5_fields_mixed32<NQ>(W[0], W[1], W[2], W[3], W[4], variant, eps, ct, WRm, WLm);
@@ -393,9 +414,10 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
             hllc<NF, ND, DIR, MODE_MIXED>(WLprev, WRm, mL, mR, C, F, uf, bad);
             if (m >= s0 + 1) {
                 // finish cell m - 1 (window slot 1); its accumulator and q^n are
-                // in update slot g, its state in state slot g - 3
+                // in the update slot (U(g)), its state in state slot g - 3
+                cp_async_wait<1>();     // U(g) done; S(g + 1) may be in flight
                 const int64_t off = base + (m - 1) * S;
-                const int us = (int)(g % kStageU), qs = (int)((g - 3) % kStageQ);
+                const int qs = (int)((g - 3) % kStageQ);
                 const R du = uf - uprev;
                 R Kc = R(0);
                 if constexpr (NF == 2) {
@@ -407,19 +429,21 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
                     const R ac = (k >= L::A && C.model == 1) ? W[1][k] + Kc : W[1][k];
                     if (k >= L::A) t = t + ac * du * inv_dx;
                     const int64_t o = off + k * C.fstride;
-                    const float Lf = acc ? *RF(us, k) + t : t;
+                    const float Lf = acc ? *RF(k) + t : t;
                     if (A.out_kind == 3) {
                         A.rhsf[o] = Lf;
                         continue;
                     }
-                    const double Lc = double(Lf);
+                    // the widening off the float64 pipe pays where the three-term update
+                    // loads that pipe; the one-term update (q1 = q + dt L) keeps the instruction
+                    const double Lc = upd2 ? f64_of_f32(Lf) : double(Lf);
                     const double qc = *Q(qs, k);
                     if (A.out_kind == 0) {
                         A.rhs[o] = Lc;
                     } else if (A.out_kind == 1) {
                         A.qout[o] = qc + dtv * Lc;
                     } else {
-                        A.qout[o] = A.rk_a * *QN(us, k) + A.rk_b * (qc + dtv * Lc);
+                        A.qout[o] = A.rk_a * *QN(k) + A.rk_b * (qc + dtv * Lc);
                     }
                 }
             }
@@ -433,14 +457,15 @@ __device__ __forceinline__ void sweep_body_staged(const Consts& C, const SweepAr
         for (int s = 0; s < 4; ++s)
 #pragma unroll
             for (int k = 0; k < NQ; ++k) W[s][k] = W[s + 1][k];
+        issue_update(g + 1);  // U(g + 1) into the slot this iteration's update has read
     }
     cp_async_wait<0>();
     if (bad) atomicOr(A.flag, 1);
 }
 
-// Eight 64-thread blocks per SM (16 warps) at 128 registers where the rings
-// fit (the sweeps that read no q^n), seven otherwise; fewer warps left the
-// march's dependency stalls exposed (8 warps: issue active 36-39 %).
+// Eight 64-thread blocks per SM (16 warps) at 128 registers, the rings of
+// eight blocks fitting an SM; fewer warps left the march's dependency stalls
+// exposed (8 warps: issue active 36-39 %).
 template <int NF, int ND, int DIR>
 __global__ void __launch_bounds__(64, 8) sweep_kernel_staged(const Consts C, const SweepArgs A) {
     sweep_body_staged<NF, ND, DIR>(C, A);
@@ -507,6 +532,17 @@ __device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A
         prim_for_recon<NF, ND, MODE, R>(qc, out, C, b);
         bad |= need && b;
     };
+    // the mixed mode brings the chunk after the next into L1 one iteration
+    // before load_prim reads it (the same clamped, boundary-mapped cells), so
+    // that its loads do not wait on L2 or HBM
+    auto prefetch_l1 = [&](int64_t c) {
+        c = c < -3 ? -3 : (c > n + 2 ? n + 2 : c);
+        bool flip = false;
+        const int64_t cc = bc_source(c, n, bclo, bchi, flip);
+        const double* p = A.q + base + cc * S;
+#pragma unroll
+        for (int f = 0; f < NQ; ++f) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + f * C.fstride));
+    };
 
     int64_t c0 = s0 - 1;
     R Wp[NQ], Wc[NQ], Wn[NQ];
@@ -514,6 +550,9 @@ __device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A
     load_prim(c0 - 32 + (lane < 30 ? 30 : lane), Wp);
     load_prim(c0 + lane, Wc);
     load_prim(c0 + 32 + lane, Wn);
+    if constexpr (MODE == MODE_MIXED) {
+        if (c0 + 32 <= s1) prefetch_l1(c0 + 64 + lane);
+    }
     R VRp[NQ], Fp[NQ], ufp = R(0);
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -652,12 +691,15 @@ __device__ __forceinline__ void sweep_x_body(const Consts& C, const SweepArgs& A
         ufp = uf;
         c0 += 32;
         if (c0 <= s1) load_prim(c0 + 32 + lane, Wn);
+        if constexpr (MODE == MODE_MIXED) {
+            if (c0 + 32 <= s1) prefetch_l1(c0 + 64 + lane);
+        }
     }
     if (bad) atomicOr(A.flag, 1);
 }
 
 template <int NF, int ND, int MODE>
-__global__ void __launch_bounds__(128) sweep_x_kernel(const Consts C, const SweepArgs A) {
+__global__ void __launch_bounds__(128, (MODE == MODE_MIXED ? 5 : 1)) sweep_x_kernel(const Consts C, const SweepArgs A) {
     sweep_x_body<NF, ND, MODE>(C, A);
 }
 

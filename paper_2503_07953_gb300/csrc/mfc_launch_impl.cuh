@@ -62,7 +62,7 @@ void launch_sweep_staged(int64_t threads, const Consts& C, const SweepArgs& A, c
     constexpr int smem_max = staged_smem_bytes<Lay<NF, ND>::NQ>(kStagedBlock, true);
     static_assert(smem_max <= 48 * 1024, "staged sweep rings must fit the default shared-memory limit");
     const int smem = staged_smem_bytes<Lay<NF, ND>::NQ>(kStagedBlock, A.out_kind == 2);
-    // the largest shared-memory carveout, so that seven or eight blocks' rings fit an SM
+    // the largest shared-memory carveout, so that eight blocks' rings fit an SM
     static const cudaError_t carve = cudaFuncSetAttribute(
         sweep_kernel_staged<NF, ND, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     (void)carve;
