@@ -24,8 +24,12 @@ constexpr size_t vjp_smem_bytes(int block) {
     return MODE == MODE_MIXED ? size_t(16 * Lay<NF, ND>::NQ + 8) * block * sizeof(float) : 0;
 }
 
+// The float32 mode is bound by latency, not by a pipe: it asks for seven
+// blocks per SM (128 registers, a few spilled; its rings allow seven), where
+// the unconstrained 251 registers left four (six blocks at 167 registers
+// measure the same).
 template <int NF, int ND, int DIR, int MODE>
-__global__ void __launch_bounds__(64) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
+__global__ void __launch_bounds__(64, (MODE == MODE_MIXED ? 7 : 1)) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
     using L = Lay<NF, ND>;
     using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
