@@ -27,9 +27,11 @@ constexpr size_t vjp_smem_bytes(int block) {
 // The float32 mode is bound by latency, not by a pipe: it asks for seven
 // blocks per SM (128 registers, a few spilled; its rings allow seven), where
 // the unconstrained 251 registers left four (six blocks at 167 registers
-// measure the same).
+// measure the same).  The double-float mode asks for six (168 registers,
+// its spills staying in L1), 3 % faster than four at 255; the float64
+// modes are bound by the float64 pipe and keep the compiler's choice.
 template <int NF, int ND, int DIR, int MODE>
-__global__ void __launch_bounds__(64, (MODE == MODE_MIXED ? 7 : 1)) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
+__global__ void __launch_bounds__(64, (MODE == MODE_MIXED ? 7 : (MODE == MODE_DF ? 6 : 1))) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
     using L = Lay<NF, ND>;
     using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
