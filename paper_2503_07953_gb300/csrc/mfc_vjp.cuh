@@ -31,7 +31,8 @@ constexpr size_t vjp_smem_bytes(int block) {
 // its spills staying in L1), 3 % faster than four at 255; the float64
 // modes are bound by the float64 pipe and keep the compiler's choice.
 template <int NF, int ND, int DIR, int MODE>
-__global__ void __launch_bounds__(64, (MODE == MODE_MIXED ? 7 : (MODE == MODE_DF ? 6 : 1))) sweep_vjp_kernel(const Consts C, const VjpArgs A) {
+__global__ void __launch_bounds__(64, (MODE == MODE_MIXED ? 7 : (MODE == MODE_DF ? 6 : 1)))
+    sweep_vjp_kernel(const Consts C, const VjpArgs A) {
     using L = Lay<NF, ND>;
     using R = typename ModeT<MODE>::R;
     constexpr int NQ = L::NQ;
